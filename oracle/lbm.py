@@ -1,0 +1,288 @@
+"""Oracle: the (2+1)-D relativistic lattice Boltzmann step for a massless fluid.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Plain FP64 numpy,
+vectorised over sites, no blocking or fusion beyond what the method states.
+
+Per time step and site (the per-site algorithm that closes Sec. 2, kept in
+the source as a commented-out subsection, and Eq. discrete-rbe):
+  1. pull-stream: f_i(x, t+1) = f*_i(x - n_i, t), with the boundary rules below;
+  2. moments N^a = sum_i f_i p_i^a, T^ab = sum_i f_i p_i^a p_i^b;
+  3. Landau frame: eps U^a = T^ab U_b gives eps and U = gamma (1, u);
+  4. n = U_a N^a;
+  5. massless equation of state eps = 2 P = 2 n T, so T = eps / (2 n);
+  6. f_i^eq = w_i (n/T) sum_k a^(k)(U, T) J^(k)(p_i)   (Eq. feq-expansion-discrete);
+  7. forcing term F_i^ext (Sec. 2.4, reading below);
+  8. f*_i = f_i - (p_i^m U_m / (p_i^0 tau)) (f_i - f_i^eq) + F_i^ext.
+
+Storage reading: the state holds deviations delta_i = f_i - w_i from the rest
+equilibrium (n = T = 1, u = 0, where f^eq_i = w_i exactly).  This is the same
+arithmetic as storing f, except that moment sums over small deviations do not
+round against the O(1) rest values:
+  * N = (1, 0, 0) + sum_i delta_i p_i and T = diag(2, 1, 1) + sum_i delta_i p_i p_i,
+    the rest values being the equilibrium moments n U and (eps + P) U U - P eta
+    at n = T = 1, u = 0, which the quadrature reproduces exactly;
+  * f^eq_i - w_i = w_i [ (n/T) (Q_i - 1) + (n - T) / T ], Q_i = sum_k a^(k) J^(k)(p_i),
+    with Q_i - 1 summed over k >= 1 (a^(0) J^(0) = 1).
+
+Readings of points the paper leaves open (each also listed in the design notes):
+  * Units: dt = 1, a hop is 5 sites, so c = 5 sites per step.
+  * Relaxation sign: relax towards f^eq as in Eq. discrete-rbe.
+  * Equation of state: massless, eps = 2 n T.
+  * Eigenvalue: the timelike eigenvector (largest eigenvalue) of T^a_b,
+    found by Newton's method on eps - E + M.u(eps) = 0 with
+    u(eps) = (Pi + eps I)^-1 M, E = T^00, M = T^0i, Pi = T^ij, from eps0 = E.
+  * Forcing: force F per particle, on-shell kinetic equation
+    d_t f + v.grad f + F.grad_p f = C; with f ~ f^eq = omega (n/T) Q the
+    source is S_i = w_i (n/T) [ (F.v_i)(Q_i - dQ/dp0) - F.grad_xy Q ] evaluated
+    at p_i (grad_p omega = -omega v for omega ~ exp(-p0)).  It is added after
+    relaxation, computed from the same (pre-force) n, u, T.
+  * Walls: a pull whose source lies outside the rectangle (and not in a
+    contact strip) takes the post-collision population of the opposite
+    direction, same shell, at the destination site (on-site bounce-back).
+  * Contacts: a strip 5 sites deep outside the edge, over the contact span,
+    whose populations are fixed at the equilibrium of (n_c, u_n * inward
+    normal, T_c); a pull from the strip takes that value.  A contact wins
+    over the wall.
+  * Initial state: the stored post-collision state at t = 0 is f^eq of the
+    initial fields; step 1 starts with streaming.
+  * Macroscopic fields at time t are the moments of the streamed populations
+    at t (the values the next collision uses).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import expansion, quadrature
+
+N_REST = np.array([1.0, 0.0, 0.0])
+T_REST = np.diag([2.0, 1.0, 1.0])
+
+
+class Tables:
+    """Per-population constants derived from the refined quadrature."""
+
+    def __init__(self):
+        q = quadrature.quadrature()
+        self.w = q["w"]
+        self.P = np.array([q["P0"], q["PX"], q["PY"]])             # p_i^a, [3, 48]
+        self.v = self.P[1:] / self.P[0]                              # unit velocities, [2, 48]
+        J = expansion.polynomials(self.P[0], self.P[1], self.P[2])
+        self.J = np.array(J)                                         # [16, 48]
+        grads = expansion.polynomial_gradients(self.P[0], self.P[1], self.P[2])
+        self.dJ = np.array([[np.broadcast_to(g[c], (quadrature.Q,)) for g in grads]
+                            for c in range(3)])                     # [3, 16, 48]
+        d = np.repeat(np.arange(quadrature.NDIR), quadrature.NSHELL)
+        j = np.tile(np.arange(quadrature.NSHELL), quadrature.NDIR)
+        self.opposite = quadrature.NSHELL * quadrature.OPPOSITE_DIR[d] + j
+        self.hop = quadrature.HOPS[d]                                # [48, 2]
+
+
+_TABLES = None
+
+
+def tables() -> Tables:
+    global _TABLES
+    if _TABLES is None:
+        _TABLES = Tables()
+    return _TABLES
+
+
+# ---------------------------------------------------------------------------
+# Local (per-site) operations; fields have any trailing shape.
+# ---------------------------------------------------------------------------
+
+def moments(delta):
+    """Deviations of N^a and T^ab from their rest values: (dN [3,...], dT [3,3,...])."""
+    t = tables()
+    dN = np.tensordot(t.P, delta, axes=(1, 0))
+    PP = t.P[:, None, :] * t.P[None, :, :]
+    dT = np.tensordot(PP, delta, axes=(2, 0))
+    return dN, dT
+
+
+def landau(dN, dT, max_iter=60):
+    """Solve eps U^a = T^ab U_b and return (n, ux, uy, T, eps)."""
+    E = 2.0 + dT[0, 0]
+    Mx, My = dT[0, 1], dT[0, 2]
+    Pxx, Pxy, Pyy = 1.0 + dT[1, 1], dT[1, 2], 1.0 + dT[2, 2]
+
+    def velocity(eps):
+        a, c = Pxx + eps, Pyy + eps
+        det = a * c - Pxy * Pxy
+        return (c * Mx - Pxy * My) / det, (a * My - Pxy * Mx) / det
+
+    eps = np.array(E, dtype=np.float64, copy=True)
+    for _ in range(max_iter):
+        ux, uy = velocity(eps)
+        g = eps - E + Mx * ux + My * uy
+        step = g / (1.0 - ux * ux - uy * uy)
+        eps = eps - step
+        if np.all(np.abs(step) <= 1e-17 * np.abs(eps)):
+            break
+    ux, uy = velocity(eps)
+    gamma = 1.0 / np.sqrt(1.0 - ux * ux - uy * uy)
+    n = gamma * ((1.0 + dN[0]) - ux * dN[1] - uy * dN[2])
+    T = eps / (2.0 * n)
+    return n, ux, uy, T, eps
+
+
+def equilibrium_deviation(n, ux, uy, T):
+    """f^eq_i - w_i for the fields (n, u, T); returns [48, ...]."""
+    t = tables()
+    a = np.array(expansion.projections(ux, uy, T))                  # [16, ...]
+    Qm1 = np.tensordot(t.J[1:].T, a[1:], axes=(1, 0))              # sum_{k>=1} a_k J_k(p_i)
+    return t.w.reshape((-1,) + (1,) * np.ndim(n)) * ((n / T) * Qm1 + (n - T) / T)
+
+
+def equilibrium(n, ux, uy, T):
+    """Full f^eq_i = w_i (n/T) sum_k a^(k) J^(k)(p_i) (Eq. feq-expansion-discrete)."""
+    t = tables()
+    a = np.array(expansion.projections(ux, uy, T))
+    Qf = np.tensordot(t.J.T, a, axes=(1, 0))
+    return t.w.reshape((-1,) + (1,) * np.ndim(n)) * (n / T) * Qf
+
+
+def forcing(n, ux, uy, T, Fx, Fy):
+    """F_i^ext for a force F per particle and dt = 1; returns [48, ...]."""
+    t = tables()
+    a = np.array(expansion.projections(ux, uy, T))
+    ex = (1,) * np.ndim(n)
+    Q = np.tensordot(t.J.T, a, axes=(1, 0))
+    dQ0 = np.tensordot(t.dJ[0].T, a, axes=(1, 0))
+    dQx = np.tensordot(t.dJ[1].T, a, axes=(1, 0))
+    dQy = np.tensordot(t.dJ[2].T, a, axes=(1, 0))
+    Fv = Fx * t.v[0].reshape((-1,) + ex) + Fy * t.v[1].reshape((-1,) + ex)
+    return t.w.reshape((-1,) + ex) * (n / T) * (Fv * (Q - dQ0) - (Fx * dQx + Fy * dQy))
+
+
+def collide(delta, tau, Fx=0.0, Fy=0.0):
+    """Relaxation + forcing of Eq. discrete-rbe on streamed deviations [48, ...]."""
+    t = tables()
+    dN, dT = moments(delta)
+    n, ux, uy, T, _ = landau(dN, dT)
+    deq = equilibrium_deviation(n, ux, uy, T)
+    ex = (1,) * np.ndim(n)
+    gamma = 1.0 / np.sqrt(1.0 - ux * ux - uy * uy)
+    # p_i^m U_m / (p_i^0 tau), U_m = gamma (1, -u) (indices lowered with eta)
+    pU = gamma * (t.P[0].reshape((-1,) + ex) - t.P[1].reshape((-1,) + ex) * ux
+                  - t.P[2].reshape((-1,) + ex) * uy)
+    omega = pU / (t.P[0].reshape((-1,) + ex) * tau)
+    out = delta - omega * (delta - deq)
+    if Fx != 0.0 or Fy != 0.0:
+        out = out + forcing(n, ux, uy, T, Fx, Fy)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Geometry and streaming
+# ---------------------------------------------------------------------------
+
+class Lattice:
+    """Rectangle [0, nx) x [0, ny), periodic or walled per axis, plus contacts.
+
+    `sample` is any object with nx, ny, periodic_x, periodic_y, tau, Fx, Fy
+    and a list `contacts` of objects with edge, x0, length, u_n, n, T.
+    """
+
+    def __init__(self, sample):
+        self.nx, self.ny = int(sample.nx), int(sample.ny)
+        self.px, self.py = bool(sample.periodic_x), bool(sample.periodic_y)
+        self.tau = float(sample.tau)
+        self.Fx, self.Fy = float(sample.Fx), float(sample.Fy)
+        self.contacts = list(sample.contacts)
+        for c in self.contacts:
+            if c.edge in (0, 1) and self.py or c.edge in (2, 3) and self.px:
+                raise ValueError("contact on a periodic edge")
+        self._build_pull_tables()
+
+    def contact_deviation(self, c):
+        normal = {0: (0.0, 1.0), 1: (0.0, -1.0), 2: (1.0, 0.0), 3: (-1.0, 0.0)}[c.edge]
+        ux, uy = c.u_n * normal[0], c.u_n * normal[1]
+        return equilibrium_deviation(np.float64(c.n), np.float64(ux), np.float64(uy),
+                                     np.float64(c.T))
+
+    def _contact_of(self, sx, sy):
+        """Index of the contact whose ghost strip holds (sx, sy), else -1."""
+        owner = np.full(sx.shape, -1, dtype=np.int64)
+        for k, c in enumerate(self.contacts):
+            lo, hi = c.x0, c.x0 + c.length
+            if c.edge == 0:
+                m = (sy < 0) & (sx >= lo) & (sx < hi)
+            elif c.edge == 1:
+                m = (sy >= self.ny) & (sx >= lo) & (sx < hi)
+            elif c.edge == 2:
+                m = (sx < 0) & (sy >= lo) & (sy < hi)
+            else:
+                m = (sx >= self.nx) & (sy >= lo) & (sy < hi)
+            owner = np.where((owner < 0) & m, k, owner)
+        return owner
+
+    def _build_pull_tables(self):
+        t = tables()
+        Y, X = np.meshgrid(np.arange(self.ny), np.arange(self.nx), indexing="ij")
+        self.pull = []
+        for i in range(quadrature.Q):
+            dx, dy = t.hop[i]
+            sx, sy = X - dx, Y - dy
+            if self.px:
+                sx = np.mod(sx, self.nx)
+            if self.py:
+                sy = np.mod(sy, self.ny)
+            inside = (sx >= 0) & (sx < self.nx) & (sy >= 0) & (sy < self.ny)
+            owner = np.where(inside, -1, self._contact_of(sx, sy))
+            wall = ~inside & (owner < 0)
+            self.pull.append((inside, np.clip(sx, 0, self.nx - 1),
+                              np.clip(sy, 0, self.ny - 1), owner, wall))
+        self.ghost = np.array([self.contact_deviation(c) for c in self.contacts]) \
+            if self.contacts else np.zeros((0, quadrature.Q))
+
+    def stream(self, post):
+        """Pull-streaming with periodic wrap, contacts and bounce-back walls."""
+        t = tables()
+        out = np.empty_like(post)
+        for i in range(quadrature.Q):
+            inside, sx, sy, owner, wall = self.pull[i]
+            v = post[i][sy, sx]
+            if len(self.contacts):
+                v = np.where(owner >= 0, self.ghost[np.maximum(owner, 0), i], v)
+            v = np.where(wall, post[t.opposite[i]], v)
+            out[i] = v
+        return out
+
+
+# ---------------------------------------------------------------------------
+# Driver
+# ---------------------------------------------------------------------------
+
+def init(lat: Lattice, n, ux, uy, T):
+    """Post-collision state at t = 0: f^eq of the initial fields (deviations)."""
+    return equilibrium_deviation(np.asarray(n, np.float64), np.asarray(ux, np.float64),
+                                 np.asarray(uy, np.float64), np.asarray(T, np.float64))
+
+
+def step(lat: Lattice, post):
+    """One time step: stream then collide.  Returns the new post-collision state."""
+    return collide(lat.stream(post), lat.tau, lat.Fx, lat.Fy)
+
+
+def run(lat: Lattice, post, nsteps):
+    for _ in range(nsteps):
+        post = step(lat, post)
+    return post
+
+
+def macroscopic(lat: Lattice, post):
+    """(n, ux, uy, T) at the current time: moments of the streamed populations."""
+    dN, dT = moments(lat.stream(post))
+    n, ux, uy, T, _ = landau(dN, dT)
+    return n, ux, uy, T
+
+
+def residual(u_prev, u_now):
+    """r = ||u(t) - u(t-1)||_2 / ||u(t)||_2 over all sites (the paper defines no
+    convergence measure; this is the reading used throughout)."""
+    dx = u_now[0] - u_prev[0]
+    dy = u_now[1] - u_prev[1]
+    num = np.sqrt(np.sum(dx * dx + dy * dy))
+    den = np.sqrt(np.sum(u_now[0] ** 2 + u_now[1] ** 2))
+    return num / den if den > 0 else (0.0 if num == 0 else np.inf)
