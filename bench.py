@@ -1,0 +1,352 @@
+"""Benchmark of the fused relativistic LBM step (GLUPS and fraction of HBM peak).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f32|f64|f16dev|bf16dev]
+                    [--impl ours|reference] [--no-cpu-baseline]
+
+Workload: the graphene-like sample, 1024 x 512 sites, no-slip walls, injector
+and collector contacts 32 sites wide on the y = 0 edge with centres 256 apart,
+uniform body force 1e-6 along the edge, tau = 1, started from n = T = 1,
+u = 0 (synthetic; the paper has no dataset).  One bench step is one time step
+of the whole domain: pull-streaming with walls and contacts, moments, Landau
+solve, equilibrium, forcing and relaxation, all in one kernel launch.
+
+L2: the working set of one step (read 48 planes, write 48 planes) is larger
+than L2 only in FP64, so a buffer larger than L2 is written before every
+timed step and each step is timed alone with CUDA events on the library's
+stream; `value` sums those device times.
+
+e2e: the same metric through the C ABI with pinned host buffers: upload of
+the initial fields, the K steps and the read-back of (n, u_x, u_y, T), all
+inside the timed region.
+
+N > 1 (torchrun): the sample is one coupled domain, so every rank runs an
+independent replica ("replicas only"); value = total site updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+WORKLOAD = ("graphene sample 1024x512, walls, 2 contacts 32 wide 256 apart on y=0, "
+            "F=1e-6 along x, tau=1, from rest")
+METRIC = "GLUPS and % HBM peak"
+L2_BYTES = 135_528_448
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--prec", default="f32", choices=sorted(BYTES))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM)), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1804_02418_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(prec)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs (the reference arm and the cpu_baseline of our line)
+# ---------------------------------------------------------------------------
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import lbm
+from paper_1804_02418_gb300 import workloads as W
+nx, ny, steps, warm = {nx}, {ny}, {steps}, {warm}
+s = W.graphene_sample() if (nx, ny) == (1024, 512) else W.graphene_sample(
+    nx=nx, ny=ny, contact_width=max(2, 32 * nx // 1024), contact_spacing=max(4, 256 * nx // 1024))
+lat = lbm.Lattice(s)
+post = lbm.init(lat, *W.rest_fields(s))
+for _ in range(warm):
+    post = lbm.step(lat, post)
+times = []
+for _ in range(steps):
+    t0 = time.perf_counter()
+    post = lbm.step(lat, post)
+    times.append(time.perf_counter() - t0)
+print(json.dumps(dict(sites=nx * ny, times=times)))
+"""
+
+
+def run_oracle(nx, ny, steps, warm):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, nx=nx, ny=ny, steps=steps, warm=warm)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(steps):
+    d = run_oracle(1024, 512, steps, 0)
+    t = sum(d["times"])
+    return {"value": d["sites"] * len(d["times"]) / t / 1e9, "unit": "GLUPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{len(d['times'])} full steps of the 1024x512 workload, FP64 numpy, "
+                      f"1 thread, {t:.1f} s"}
+
+
+def reference_arm(args):
+    ladder = [(1024, 512), (512, 256), (256, 128), (128, 64), (64, 32), (32, 16)]
+    budget = 150.0
+    chosen = ladder[-1]
+    for nx, ny in ladder:
+        probe = run_oracle(nx, ny, 1, 0)
+        if probe["times"][0] * (args.steps + args.warmup) <= budget:
+            chosen = (nx, ny)
+            break
+    d = run_oracle(chosen[0], chosen[1], args.steps, args.warmup)
+    t = sum(d["times"])
+    value = d["sites"] * args.steps / t / 1e9
+    sample = (f"{args.steps} oracle steps of the same geometry scaled to {chosen[0]}x{chosen[1]} "
+              f"(bounded so the run ends within minutes), FP64 numpy, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_arm(args, rank, world, cpu_line):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1804_02418_gb300 import build, rlbm, workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    s = W.graphene_sample()
+    sites = s.sites
+    stream = torch.cuda.Stream()
+    sv = rlbm.Solver(s, prec=args.prec, stream=stream)
+    flush = torch.empty(max(2 * L2_BYTES, 256 << 20), dtype=torch.uint8, device="cuda")
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    # -- device-timed region: K single steps, L2 flushed before each ----------
+    with torch.cuda.stream(stream):
+        sv.init(0)
+        for _ in range(args.warmup):
+            flush.zero_()
+            sv.step(1)
+    sync_all()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = sv.launches
+    sync_all()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sv.step(1)
+            ev[k][1].record(stream)
+    sync_all()
+    launches = sv.launches - l0
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    sv.check()
+    t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_ms = float(t.item())
+
+    # -- end to end through the C ABI with pinned host buffers ----------------
+    host_in = [torch.ones((s.ny, s.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    host_in[1].zero_()
+    host_in[2].zero_()
+    host_out = [torch.empty((s.ny, s.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    sync_all()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sv.init(0, *host_in)
+    sv.step(args.steps)
+    sv.moments(0, out=host_out)
+    e1.record(stream)
+    sync_all()
+    e2e_ms = e0.elapsed_time(e1)
+    t2 = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t2.item())
+    finite = bool(np.isfinite(host_out[1].numpy()).all())
+    sv.close()
+
+    if rank != 0:
+        return
+    hbm, hbm_kind = peaks()
+    alg_bytes = 2 * 48 * BYTES[args.prec] * sites
+    avg_launch_s = t_ms / 1e3 / args.steps
+    achieved = alg_bytes / avg_launch_s / 1e9
+    value = world * sites * args.steps / (t_ms / 1e3) / 1e9
+    field_bytes = 4 * 8 * sites
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "f32": "f32", "f16dev": "f16 storage / f32 compute",
+                  "bf16dev": "bf16 storage / f32 compute"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.prec, "sites": sites,
+                   "l2": "buffer of 2x L2 written before every timed step; steps timed alone",
+                   "parallelism": "replicas only" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": ncu_traffic(args.prec),
+                     "peak_kind": hbm_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": {"value": world * sites * args.steps / (e2e_ms / 1e3) / 1e9, "unit": "GLUPS",
+                "h2d_bytes_per_step": field_bytes / args.steps,
+                "d2h_bytes_per_step": field_bytes / args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "fields_finite": finite,
+    }
+    if cpu_line is not None:
+        line["cpu_baseline"] = cpu_line
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        return
+    # the CPU oracle runs before any CUDA call of this process
+    cpu_line = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_line = cpu_baseline(args.cpu_sample_steps)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    try:
+        gpu_arm(args, rank, world, cpu_line)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

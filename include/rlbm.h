@@ -1,0 +1,173 @@
+/*
+ * rlbm.h - C ABI of the GB300 relativistic lattice Boltzmann library.
+ *
+ * The library advances the (2+1)-dimensional relativistic lattice Boltzmann
+ * method for a massless fluid of Gabbana, Mendoza, Succi and Tripiccione
+ * (arXiv:1804.02418) on one GPU:
+ *   - discrete relativistic BGK update, Eq. discrete-rbe (Sec. 2.2):
+ *       f_i(x + v_i dt, t + dt) - f_i(x, t)
+ *         = -dt (p_i^m U_m / (p_i^0 tau)) (f_i - f_i^eq) + F_i^ext ;
+ *   - per-site algorithm (end of Sec. 2): moments N^a, T^ab; Landau frame
+ *     eps U^a = T^ab U_b; n = U_a N^a; massless equation of state
+ *     eps = 2 n T; equilibrium f_i^eq = w_i (n/T) sum_k a^(k) J^(k)(p_i)
+ *     (Eq. feq-expansion-discrete, App. A-B); forcing term (Sec. 2.4);
+ *   - the 48-population stencil G = {(+-3,+-4)_FS, (+-5,0)_FS} with four
+ *     energy shells (Sec. 2.3), weights refined onto Eq. orthonormal;
+ *   - bounce-back walls and non-evolving injector / collector contacts
+ *     (Sec. 3, Fig. geom caption).
+ *
+ * Units: dt = 1, one hop is 5 sites (c = 5 sites per step), a force is the
+ * momentum given to one particle per step.
+ *
+ * Population index i = 4 d + j (direction d = 0..11, shell j = 0..3) with
+ * directions (3,4) (-3,-4) (-3,4) (3,-4) (4,3) (-4,-3) (-4,3) (4,-3)
+ * (5,0) (-5,0) (0,5) (0,-5); the opposite of direction d is d ^ 1.
+ *
+ * Fields exchanged with the caller are FP64, row-major [ny][nx] (x fastest),
+ * dense (row stride nx).  Pointers are host pointers when device_ptrs == 0
+ * and device pointers on the context's device when device_ptrs != 0.  The
+ * caller owns every array it passes; the context owns (or borrows, see
+ * rlbm_config.workspace) the population buffers.
+ *
+ * Errors: every int-returning call returns RLBM_OK (0) or a negative code;
+ * rlbm_last_error() then holds a message.  A context is not thread-safe;
+ * distinct contexts are independent.  All device work is issued on the
+ * stream given in rlbm_config (default stream if NULL).  Calls that return
+ * data to host memory synchronise that stream.
+ */
+#ifndef RLBM_H
+#define RLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RLBM_Q 48
+#define RLBM_MAX_CONTACTS 4
+#define RLBM_HOP_RADIUS 5
+
+enum {
+  RLBM_OK = 0,
+  RLBM_EINVAL = -1,    /* bad argument: dims < 11, tau <= 0.5, |F| >= 1e-2, bad contact, ... */
+  RLBM_ENOMEM = -2,    /* device allocation failed or workspace too small */
+  RLBM_ECUDA = -3,     /* a CUDA runtime call failed */
+  RLBM_ENAN = -4,      /* device error word set: non-finite field, |u| >= 1 or
+                          no convergence of the Landau solve */
+  RLBM_ETIMEOUT = -5,  /* a bounded device wait gave up */
+  RLBM_ESTATE = -6     /* call out of order (e.g. step before init) */
+};
+
+/* Storage / arithmetic precision of the populations.
+ * RLBM_F64:    FP64 storage of f_i - w_i, FP64 arithmetic.
+ * RLBM_F32:    FP32 storage of f_i - w_i, FP32 arithmetic.
+ * RLBM_F16DEV: FP16 storage of the scaled relative deviation
+ *              g_i = s (f_i - w_i) / w_i, FP32 arithmetic.
+ * RLBM_BF16DEV: as RLBM_F16DEV with BF16 storage. */
+typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_F16DEV = 2, RLBM_BF16DEV = 3 } rlbm_prec;
+
+/* A contact (Sec. 3): `length` sites of edge `edge` starting at `x0`
+ * (edge 0: y = 0, 1: y = ny-1, 2: x = 0, 3: x = nx-1; x0 runs along x for
+ * edges 0/1 and along y for edges 2/3).  It is a ghost strip 5 sites deep
+ * outside that edge whose populations stay at the equilibrium of
+ * (n, u_n * inward normal, T).  A pull whose source lies in the strip reads
+ * that value; every other pull from outside the rectangle bounces back. */
+typedef struct {
+  int edge;
+  int x0;
+  int length;
+  double u_n;
+  double n;
+  double T;
+} rlbm_contact;
+
+/* One sample: an nx x ny rectangle, periodic or walled per axis, relaxation
+ * time tau (> 0.5), uniform body force (Fx, Fy) per particle, contacts. */
+typedef struct {
+  int nx, ny;
+  int periodic_x, periodic_y;
+  double tau;
+  double Fx, Fy;
+  int ncontacts;
+  rlbm_contact contacts[RLBM_MAX_CONTACTS];
+} rlbm_sample;
+
+typedef struct {
+  rlbm_prec prec;
+  int nsamples;                 /* >= 1; all samples advance together */
+  const rlbm_sample* samples;   /* array of nsamples, copied by rlbm_create */
+  void* stream;                 /* cudaStream_t, or NULL for the default stream */
+  void* workspace;              /* optional device buffer of >= rlbm_workspace_size()
+                                   bytes, 256-byte aligned, borrowed (not freed);
+                                   NULL: the context allocates its own */
+  size_t workspace_bytes;
+} rlbm_config;
+
+typedef struct rlbm_ctx rlbm_ctx;
+
+/* Bytes of device memory a context needs for cfg (populations: two buffers of
+ * 48 planes per sample; plus residual and staging scratch).  Host only. */
+int rlbm_workspace_size(const rlbm_config* cfg, size_t* bytes);
+
+/* Validates cfg, derives the refined quadrature, uploads constants and binds
+ * or allocates the workspace.  The populations are undefined until
+ * rlbm_init / rlbm_set_state.  On failure *out is NULL. */
+int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out);
+
+/* Sets the stored (post-collision) state of `sample` to f^eq of the given
+ * fields (Eq. feq-expansion-discrete).  NULL field pointers mean the rest
+ * state n = T = 1, u = 0 (all four must then be NULL).  |u| < 1, n, T > 0. */
+int rlbm_init(rlbm_ctx* ctx, int sample, const double* n, const double* ux,
+              const double* uy, const double* T, int device_ptrs);
+
+/* Advances every sample by nsteps >= 0 time steps (stream, then collide).
+ * If residual != NULL, the last two steps also reduce
+ *   r = ||u(t) - u(t-1)||_2 / ||u(t)||_2   over all sites of all samples
+ * (u from the streamed populations of those steps), the stream is
+ * synchronised, *residual is written and the device error word is checked
+ * (RLBM_ENAN).  Needs nsteps >= 2 in that case.  Without residual the call
+ * is asynchronous and checks nothing; use rlbm_check. */
+int rlbm_step(rlbm_ctx* ctx, int nsteps, double* residual);
+
+/* Macroscopic fields (n, u_x, u_y, T) of `sample` at the current time: the
+ * Landau-frame values of the streamed populations, i.e. those the next
+ * collision uses.  Any output pointer may be NULL. */
+int rlbm_moments(rlbm_ctx* ctx, int sample, double* n, double* ux, double* uy,
+                 double* T, int device_ptrs);
+
+/* Stored post-collision state of `sample` as deviations f_i - w_i, layout
+ * [48][ny][nx] FP64 (checkpoint / restart and one-step checks). */
+int rlbm_get_state(rlbm_ctx* ctx, int sample, double* delta, int device_ptrs);
+int rlbm_set_state(rlbm_ctx* ctx, int sample, const double* delta, int device_ptrs);
+
+/* Synchronises the stream and returns RLBM_ENAN if any kernel since the last
+ * check flagged a non-finite or unphysical site (then clears the flag). */
+int rlbm_check(rlbm_ctx* ctx);
+
+/* Number of time steps taken since the last rlbm_init / rlbm_set_state. */
+long long rlbm_steps_done(const rlbm_ctx* ctx);
+
+/* Frees what the context allocated.  NULL is a no-op. */
+void rlbm_destroy(rlbm_ctx* ctx);
+
+/* Last error message of ctx (or of the last failed rlbm_create if ctx is
+ * NULL).  Valid until the next call on ctx. */
+const char* rlbm_last_error(const rlbm_ctx* ctx);
+
+/* The refined quadrature the library uses: w1[j] for the (3,4)-type
+ * directions, w2[j] for the (5,0)-type, p0[j] the shell energies (Sec. 2.3,
+ * printed values moved onto the exact solutions of Eq. orthonormal by
+ * minimum-norm Gauss-Newton steps).  Host only; needs no GPU. */
+int rlbm_quadrature(double w1[4], double w2[4], double p0[4]);
+
+/* Kernel launches issued by this context so far (all kinds). */
+long long rlbm_launch_count(const rlbm_ctx* ctx);
+
+int rlbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLBM_H */

@@ -121,6 +121,48 @@ def projections(ux, uy, T):
     ]
 
 
+def projections_near_rest(ux, uy, dT):
+    """App. B rewritten for numerical accuracy near the rest state.
+
+    Identical algebra to projections(), with every coefficient expressed
+    through quantities that vanish at rest (n = T = 1, u = 0):
+        Tu = T u^0 - 1 = (T - 1) gamma + (gamma - 1),  gamma - 1 = u^2 / (s (1 + s)),
+        s = sqrt(1 - u^2),  T^2 - 1 = (T - 1)(T + 1),  (u^0)^2 - 1 = gamma^2 u^2,
+    and combinations such as Tu - (T^2 - 1)/2 = (gamma - 1) T - (T - 1)^2 / 2
+    written without the cancelling first-order parts, so that small
+    coefficients keep full relative precision instead of rounding against
+    O(1) terms.  dT is T - 1.
+    """
+    u2 = ux * ux + uy * uy
+    s = np.sqrt(1.0 - u2)
+    g = 1.0 / s
+    gm1 = u2 / (s * (1.0 + s))
+    T = 1.0 + dT
+    uX, uY = g * ux, g * uy
+    Tu = dT * g + gm1
+    g2 = g * g
+    xx = g2 * (uy * uy - ux * ux)            # (u^0)^2 - 2 (u^x)^2 - 1
+    xxy = g2 * (uy * uy - 3.0 * ux * ux)     # (u^0)^2 - 4 (u^x)^2 - 1
+    return [
+        np.ones_like(T),
+        Tu,
+        T * uX,
+        T * uY,
+        1.5 * Tu * Tu + gm1 * T - 0.5 * dT * dT,
+        S3 * T * uX * Tu,
+        S3 * T * uY * Tu,
+        -0.5 * S3 * T**2 * xx,
+        S3 * T**2 * uX * uY,
+        0.5 * Tu * (5.0 * Tu * Tu + 6.0 * gm1 * T - 3.0 * dT * dT),
+        0.5 * T * uX * (5.0 * T**2 * uX * uX + 3.0 * dT * dT - 6.0 * gm1 * T),
+        -0.5 * S15 * T * uX * (-2.0 * Tu * Tu + T**2 * uX * uX + dT * dT - 2.0 * gm1 * T),
+        -0.5 * S15 * T**2 * Tu * xx,
+        0.5 * S32 * T * uY * (5.0 * Tu * Tu + 2.0 * gm1 * T - dT * dT),
+        -0.5 * S52 * T**3 * uY * xxy,
+        S15 * T**2 * uX * uY * Tu,
+    ]
+
+
 def feq_appendix_c(w, p0, px, py, n, ux, uy, T):
     """The fully expanded discrete equilibrium printed in App. C (m = 0, N = 3).
 

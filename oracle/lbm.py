@@ -101,37 +101,65 @@ def moments(delta):
 
 
 def landau(dN, dT, max_iter=60):
-    """Solve eps U^a = T^ab U_b and return (n, ux, uy, T, eps)."""
-    E = 2.0 + dT[0, 0]
-    Mx, My = dT[0, 1], dT[0, 2]
-    Pxx, Pxy, Pyy = 1.0 + dT[1, 1], dT[1, 2], 1.0 + dT[2, 2]
+    """Solve eps U^a = T^ab U_b; returns (n, ux, uy, T, eps).
 
-    def velocity(eps):
-        a, c = Pxx + eps, Pyy + eps
+    Works on the deviations from rest: eps = 2 + deps with Newton on deps,
+    n - 1 and T - 1 formed without subtracting O(1) numbers, so fields near
+    rest keep full relative precision in their deviations (see landau_dev).
+    """
+    dn, ux, uy, dTT, deps = landau_dev(dN, dT, max_iter)
+    return 1.0 + dn, ux, uy, 1.0 + dTT, 2.0 + deps
+
+
+def landau_dev(dN, dT, max_iter=60):
+    """Landau frame in deviation variables: returns (n - 1, ux, uy, T - 1, eps - 2).
+
+    E = T^00 = 2 + dE, M = T^0i, Pi = T^ij = I + dPi (rest values diag(2, 1, 1)).
+    u(eps) = (Pi + eps I)^-1 M, g(eps) = eps - E + M.u(eps), g'(eps) = 1 - u.u,
+    Newton from eps0 = E.  Then n = U_a N^a = gamma (N^0 - u.N) and the
+    massless equation of state gives T = eps / (2 n).
+    """
+    dE = dT[0, 0]
+    Mx, My = dT[0, 1], dT[0, 2]
+    dPxx, Pxy, dPyy = dT[1, 1], dT[1, 2], dT[2, 2]
+
+    def velocity(deps):
+        a, c = 3.0 + dPxx + deps, 3.0 + dPyy + deps      # Pi + eps I, eps = 2 + deps
         det = a * c - Pxy * Pxy
         return (c * Mx - Pxy * My) / det, (a * My - Pxy * Mx) / det
 
-    eps = np.array(E, dtype=np.float64, copy=True)
+    deps = np.array(dE, dtype=np.float64, copy=True)
     for _ in range(max_iter):
-        ux, uy = velocity(eps)
-        g = eps - E + Mx * ux + My * uy
+        ux, uy = velocity(deps)
+        g = deps - dE + Mx * ux + My * uy
         step = g / (1.0 - ux * ux - uy * uy)
-        eps = eps - step
-        if np.all(np.abs(step) <= 1e-17 * np.abs(eps)):
+        deps = deps - step
+        if np.all(np.abs(step) <= 1e-17 * (2.0 + np.abs(deps))):
             break
-    ux, uy = velocity(eps)
-    gamma = 1.0 / np.sqrt(1.0 - ux * ux - uy * uy)
-    n = gamma * ((1.0 + dN[0]) - ux * dN[1] - uy * dN[2])
-    T = eps / (2.0 * n)
-    return n, ux, uy, T, eps
+    ux, uy = velocity(deps)
+    u2 = ux * ux + uy * uy
+    s = np.sqrt(1.0 - u2)
+    gm1 = u2 / (s * (1.0 + s))                      # gamma - 1
+    dpar = dN[0] - ux * dN[1] - uy * dN[2]          # N^0 - u.N - 1
+    dn = gm1 * (1.0 + dpar) + dpar                  # n - 1 = gamma (1 + dpar) - 1
+    dTT = (deps - 2.0 * dn) / (2.0 * (1.0 + dn))     # T - 1 = eps / (2 n) - 1
+    return dn, ux, uy, dTT, deps
 
 
-def equilibrium_deviation(n, ux, uy, T):
-    """f^eq_i - w_i for the fields (n, u, T); returns [48, ...]."""
+def equilibrium_deviation(n, ux, uy, T, dn=None, dT=None):
+    """f^eq_i - w_i for the fields (n, u, T); returns [48, ...].
+
+    dn = n - 1 and dT = T - 1 may be given for full relative precision of
+    deviations near rest (otherwise they are formed from n and T)."""
     t = tables()
-    a = np.array(expansion.projections(ux, uy, T))                  # [16, ...]
+    if dn is None:
+        dn = n - 1.0
+    if dT is None:
+        dT = T - 1.0
+    a = np.array(expansion.projections_near_rest(ux, uy, dT))       # [16, ...]
     Qm1 = np.tensordot(t.J[1:].T, a[1:], axes=(1, 0))              # sum_{k>=1} a_k J_k(p_i)
-    return t.w.reshape((-1,) + (1,) * np.ndim(n)) * ((n / T) * Qm1 + (n - T) / T)
+    nT = (1.0 + dn) / (1.0 + dT)
+    return t.w.reshape((-1,) + (1,) * np.ndim(dn)) * (nT * Qm1 + (dn - dT) / (1.0 + dT))
 
 
 def equilibrium(n, ux, uy, T):
@@ -159,8 +187,9 @@ def collide(delta, tau, Fx=0.0, Fy=0.0):
     """Relaxation + forcing of Eq. discrete-rbe on streamed deviations [48, ...]."""
     t = tables()
     dN, dT = moments(delta)
-    n, ux, uy, T, _ = landau(dN, dT)
-    deq = equilibrium_deviation(n, ux, uy, T)
+    dn, ux, uy, dTT, _ = landau_dev(dN, dT)
+    n, T = 1.0 + dn, 1.0 + dTT
+    deq = equilibrium_deviation(n, ux, uy, T, dn=dn, dT=dTT)
     ex = (1,) * np.ndim(n)
     gamma = 1.0 / np.sqrt(1.0 - ux * ux - uy * uy)
     # p_i^m U_m / (p_i^0 tau), U_m = gamma (1, -u) (indices lowered with eta)
@@ -256,8 +285,8 @@ class Lattice:
 
 def init(lat: Lattice, n, ux, uy, T):
     """Post-collision state at t = 0: f^eq of the initial fields (deviations)."""
-    return equilibrium_deviation(np.asarray(n, np.float64), np.asarray(ux, np.float64),
-                                 np.asarray(uy, np.float64), np.asarray(T, np.float64))
+    n, ux, uy, T = (np.asarray(a, np.float64) for a in (n, ux, uy, T))
+    return equilibrium_deviation(n, ux, uy, T, dn=n - 1.0, dT=T - 1.0)
 
 
 def step(lat: Lattice, post):
@@ -274,8 +303,8 @@ def run(lat: Lattice, post, nsteps):
 def macroscopic(lat: Lattice, post):
     """(n, ux, uy, T) at the current time: moments of the streamed populations."""
     dN, dT = moments(lat.stream(post))
-    n, ux, uy, T, _ = landau(dN, dT)
-    return n, ux, uy, T
+    dn, ux, uy, dTT, _ = landau_dev(dN, dT)
+    return 1.0 + dn, ux, uy, 1.0 + dTT
 
 
 def residual(u_prev, u_now):

@@ -1,0 +1,116 @@
+// Kernel module for one storage type.  Included once per translation unit
+// with RLBM_S (storage type) and RLBM_OPS (accessor name) defined; each unit
+// owns its own copy of the quadrature constants in constant memory.
+#include "kernels.cuh"
+#include "ops.h"
+
+namespace rlbm {
+namespace {
+
+using S = RLBM_S;
+using R = typename Codec<S>::R;
+
+__constant__ QuadConsts<R> c_qc;
+
+template <bool FORCE, int RES>
+__global__ void __launch_bounds__(kBX) k_step(const S* __restrict__ fin, S* __restrict__ fout,
+                                              DevSample s, const R* __restrict__ ghost,
+                                              StepAux<R> aux) {
+  step_body<S, FORCE, RES>(fin, fout, s, ghost, aux, c_qc);
+}
+
+__global__ void __launch_bounds__(kBX) k_moments(const S* __restrict__ fin, DevSample s,
+                                                 const R* __restrict__ ghost, double* n,
+                                                 double* ux, double* uy, double* T,
+                                                 unsigned* err) {
+  moments_body<S>(fin, s, ghost, n, ux, uy, T, err, c_qc);
+}
+
+__global__ void __launch_bounds__(kBX) k_init(S* __restrict__ fout, DevSample s, const double* n,
+                                              const double* ux, const double* uy,
+                                              const double* T, unsigned* err) {
+  init_body<S>(fout, s, n, ux, uy, T, err, c_qc);
+}
+
+__global__ void __launch_bounds__(kBX) k_get(const S* __restrict__ fin, DevSample s, int q0,
+                                             double* out) {
+  get_state_body<S>(fin, s, q0, out, c_qc);
+}
+
+__global__ void __launch_bounds__(kBX) k_set(S* __restrict__ fout, DevSample s, int q0,
+                                             const double* in) {
+  set_state_body<S>(fout, s, q0, in, c_qc);
+}
+
+dim3 site_grid(const DevSample& s) { return dim3((s.nx + kBX - 1) / kBX, s.ny, 1); }
+
+cudaError_t upload(const double p0[4], const double w[2][4], double scale) {
+  QuadConsts<R> h;
+  for (int j = 0; j < kShells; ++j) {
+    h.p0[j] = R(p0[j]);
+    for (int k = 0; k < 2; ++k) {
+      h.w[k][j] = R(w[k][j]);
+      h.dec[k][j] = R(w[k][j] / scale);
+      h.enc[k][j] = R(scale / w[k][j]);
+    }
+  }
+  return cudaMemcpyToSymbol(c_qc, &h, sizeof(h));
+}
+
+cudaError_t step(const void* fin, void* fout, const DevSample& s, const void* ghost, bool force,
+                 int res, void* uprev, double* acc, unsigned* err, cudaStream_t st) {
+  StepAux<R> aux{static_cast<R*>(uprev), acc, err};
+  const S* a = static_cast<const S*>(fin);
+  S* b = static_cast<S*>(fout);
+  const R* g = static_cast<const R*>(ghost);
+  const dim3 grid = site_grid(s);
+  if (force) {
+    if (res == 0) k_step<true, 0><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
+    else if (res == 1) k_step<true, 1><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
+    else k_step<true, 2><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
+  } else {
+    if (res == 0) k_step<false, 0><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
+    else if (res == 1) k_step<false, 1><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
+    else k_step<false, 2><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t moments(const void* fin, const DevSample& s, const void* ghost, double* n, double* ux,
+                    double* uy, double* T, unsigned* err, cudaStream_t st) {
+  k_moments<<<site_grid(s), kBX, 0, st>>>(static_cast<const S*>(fin), s,
+                                         static_cast<const R*>(ghost), n, ux, uy, T, err);
+  return cudaGetLastError();
+}
+
+cudaError_t init(void* fout, const DevSample& s, const double* n, const double* ux,
+                 const double* uy, const double* T, unsigned* err, cudaStream_t st) {
+  k_init<<<site_grid(s), kBX, 0, st>>>(static_cast<S*>(fout), s, n, ux, uy, T, err);
+  return cudaGetLastError();
+}
+
+cudaError_t get_state(const void* fin, const DevSample& s, int q0, int nq, double* out,
+                      cudaStream_t st) {
+  dim3 grid = site_grid(s);
+  grid.z = nq;
+  k_get<<<grid, kBX, 0, st>>>(static_cast<const S*>(fin), s, q0, out);
+  return cudaGetLastError();
+}
+
+cudaError_t set_state(void* fout, const DevSample& s, int q0, int nq, const double* in,
+                      cudaStream_t st) {
+  dim3 grid = site_grid(s);
+  grid.z = nq;
+  k_set<<<grid, kBX, 0, st>>>(static_cast<S*>(fout), s, q0, in);
+  return cudaGetLastError();
+}
+
+const PrecOps kOps = {
+    RLBM_NAME, sizeof(S), sizeof(R), upload, step, moments, init, get_state, set_state, 1,
+};
+
+}  // namespace
+
+const PrecOps* RLBM_OPS() { return &kOps; }
+
+}  // namespace rlbm

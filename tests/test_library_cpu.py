@@ -1,0 +1,115 @@
+"""Host-side checks of the C ABI library (no GPU needed).
+
+* the library builds and loads, and exports every function declared in
+  include/rlbm.h;
+* the host-only quadrature refinement agrees with the oracle's (stored in
+  tests/golden/quadrature_refined.txt by tests/golden/make_golden.py);
+* argument validation (rlbm_workspace_size touches no device).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1804_02418_gb300 import rlbm, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1804_02418_gb300 import build
+    build.build()
+    return rlbm.load_library()
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if fn.endswith(".h"):
+            src = open(os.path.join(inc, fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(rlbm_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in rlbm.EXPORTS, f"{n} has no binding"
+
+
+def test_library_quadrature_matches_oracle_golden(lib):
+    w1, w2, p0 = rlbm.quadrature()
+    g = np.loadtxt(os.path.join(ROOT, "tests", "golden", "quadrature_refined.txt"), comments="#")
+    assert np.allclose(w1, g[:, 1], rtol=1e-14, atol=0)
+    assert np.allclose(w2, g[:, 2], rtol=1e-14, atol=0)
+    # minimum-norm refinement in absolute units: the smallest shell energy
+    # (1.6e-5) is fixed to ~1e-16 absolute by either side's rounding
+    assert np.allclose(p0, g[:, 3], rtol=1e-14, atol=1e-15)
+
+
+def _cfg(samples, prec=1):
+    arr = (rlbm._Sample * len(samples))(*[rlbm._to_c_sample(s) for s in samples])
+    cfg = rlbm._Config()
+    cfg.prec = prec
+    cfg.nsamples = len(samples)
+    cfg.samples = arr
+    return cfg, arr
+
+
+def _size(lib, samples, prec=1):
+    cfg, keep = _cfg(samples, prec)
+    n = ctypes.c_size_t()
+    rc = lib.rlbm_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
+    return rc, n.value
+
+
+def test_workspace_size_counts_two_population_buffers(lib):
+    s = workloads.graphene_sample()
+    for prec, es in ((0, 8), (1, 4), (2, 2), (3, 2)):
+        rc, n = _size(lib, [s], prec)
+        assert rc == 0
+        pops = 2 * 48 * s.nx * s.ny * es
+        assert pops <= n <= pops * 1.05 + 60 * s.nx * s.ny
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=10), dict(ny=5), dict(tau=0.5), dict(tau=0.2), dict(Fx=0.02),
+])
+def test_invalid_samples_are_rejected(lib, bad):
+    s = workloads.graphene_sample(nx=64, ny=32, contact_spacing=24, contact_width=8)
+    for k, v in bad.items():
+        setattr(s, k, v)
+    rc, _ = _size(lib, [s])
+    assert rc == -1
+    assert lib.rlbm_last_error(None)
+
+
+def test_invalid_contacts_are_rejected(lib):
+    C = workloads.Contact
+    cases = [
+        workloads.Sample(32, 32, contacts=[C(0, 30, 5)]),                 # off the edge
+        workloads.Sample(32, 32, periodic_y=True, contacts=[C(0, 3, 5)]), # periodic edge
+        workloads.Sample(32, 32, contacts=[C(4, 3, 5)]),                  # no such edge
+        workloads.Sample(32, 32, contacts=[C(0, 3, 0)]),                  # empty
+    ]
+    for s in cases:
+        rc, _ = _size(lib, [s])
+        assert rc == -1
+
+
+def test_bad_precision_and_empty_config(lib):
+    s = workloads.shear_wave(16)
+    rc, _ = _size(lib, [s], prec=7)
+    assert rc == -1
+    cfg = rlbm._Config()
+    cfg.prec = 1
+    cfg.nsamples = 0
+    n = ctypes.c_size_t()
+    assert lib.rlbm_workspace_size(ctypes.byref(cfg), ctypes.byref(n)) == -1

@@ -99,3 +99,58 @@ def test_small_velocity_deviation_is_odd_and_accurate():
     Nx2 = np.sum(d2 * q["PX"])
     assert abs(Nx1 - 1e-7) < 1e-20 + 1e-13 * 1e-7
     assert abs(Nx2 / Nx1 - 2.0) < 1e-12
+
+
+def _appendix_b_mp(ux, uy, T, mp):
+    """Literal App. B in 50-digit arithmetic (reference for the near-rest form)."""
+    ux, uy, T = mp.mpf(ux), mp.mpf(uy), mp.mpf(T)
+    g = 1 / mp.sqrt(1 - ux * ux - uy * uy)
+    u0, uX, uY = g, g * ux, g * uy
+    s3, s15, s32, s52 = mp.sqrt(3), mp.sqrt(15), mp.sqrt(mp.mpf(3) / 2), mp.sqrt(mp.mpf(5) / 2)
+    Tu = T * u0 - 1
+    return [
+        mp.mpf(1), Tu, T * uX, T * uY,
+        T**2 * (3 * u0**2 - 1) / 2 - 2 * T * u0 + 1,
+        s3 * T * uX * Tu, s3 * T * uY * Tu,
+        -s3 * T**2 * (u0**2 - 2 * uX**2 - 1) / 2,
+        s3 * T**2 * uX * uY,
+        Tu * (T**2 * (5 * u0**2 - 3) - 4 * T * u0 + 2) / 2,
+        T * uX * (T**2 * (5 * uX**2 + 3) - 6 * T * u0 + 3) / 2,
+        -s15 * T * uX * (T**2 * (-2 * u0**2 + uX**2 + 1) + 2 * T * u0 - 1) / 2,
+        -s15 * T**2 * Tu * (u0**2 - 2 * uX**2 - 1) / 2,
+        s32 * T * uY * (T**2 * (5 * u0**2 - 1) - 8 * T * u0 + 4) / 2,
+        -s52 * T**3 * uY * (u0**2 - 4 * uX**2 - 1) / 2,
+        s15 * T**2 * uX * uY * Tu,
+    ]
+
+
+@pytest.mark.parametrize("state", [(3e-7, -2e-7, 5e-8), (1e-4, 2e-5, -3e-6), (0.02, -0.01, 0.003),
+                                   (0.3, 0.1, 0.2)])
+def test_near_rest_projections_equal_appendix_b_in_high_precision(state):
+    """The rearranged App. B used by the oracle equals the literal App. B
+    evaluated in 50-digit arithmetic, coefficient by coefficient, to full
+    double relative precision even where the literal double evaluation
+    cancels catastrophically."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    ux, uy, dT = state
+    ref = _appendix_b_mp(ux, uy, mp.mpf(1) + mp.mpf(dT), mp)
+    got = expansion.projections_near_rest(np.float64(ux), np.float64(uy), np.float64(dT))
+    for k in range(16):
+        r = float(ref[k])
+        assert abs(float(got[k]) - r) <= 1e-13 * abs(r) + 1e-300, (k, float(got[k]), r)
+
+
+def test_landau_recovers_small_deviations_to_full_precision():
+    rng = np.random.default_rng(9)
+    shape = (100,)
+    dn = rng.uniform(-1e-9, 1e-9, shape)
+    dT = rng.uniform(-1e-9, 1e-9, shape)
+    ux = rng.uniform(-1e-6, 1e-6, shape)
+    uy = rng.uniform(-1e-6, 1e-6, shape)
+    d = lbm.equilibrium_deviation(1.0 + dn, ux, uy, 1.0 + dT, dn=dn, dT=dT)
+    dn2, ux2, uy2, dT2, _ = lbm.landau_dev(*lbm.moments(d))
+    assert np.abs(dn2 - dn).max() < 1e-12 * np.abs(dn).max()
+    assert np.abs(dT2 - dT).max() < 1e-12 * np.abs(dT).max()
+    assert np.abs(ux2 - ux).max() < 1e-12 * np.abs(ux).max()
+    assert np.abs(uy2 - uy).max() < 1e-12 * np.abs(uy).max()
