@@ -166,6 +166,28 @@ long long rlbm_launch_count(const rlbm_ctx* ctx);
 
 int rlbm_version(void);
 
+/* Convergence residual that allocates nothing (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory when they check convergence
+ * (another framework owns the whole memory pool, a real-time loop with a
+ * memory budget fixed at start-up, a host callback where cudaMalloc is not
+ * allowed).  Computes on `stream`
+ *     *residual = ||u - u_prev||_2 / ||u||_2   (0 if both norms are 0,
+ *                                              +inf if only ||u|| is 0)
+ * over nsites sites from four caller-owned FP64 device arrays of nsites
+ * values (ux_prev, uy_prev, ux, uy) into one caller-owned device double.
+ * Scratch is a fixed 64 KiB array inside the library (one partial-sum pair
+ * per 2048 sites); nsites must be 1 .. 8,388,608, larger sizes return
+ * RLBM_EINVAL with a message in rlbm_last_error(NULL).  Calls no
+ * cudaMalloc, cudaFree or allocating library routine.  The first call on a
+ * device (with that device current) looks the scratch address up; make it
+ * before any stream capture.  All calls share the scratch: calls that
+ * overlap on the GPU race and must be serialised by the caller.  The result
+ * is the same quantity rlbm_step reports, summed in a fixed order. */
+int rlbm_velocity_residual_static(const double* ux_prev, const double* uy_prev,
+                                  const double* ux, const double* uy, long long nsites,
+                                  double* residual, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

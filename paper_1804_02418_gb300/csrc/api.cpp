@@ -90,6 +90,10 @@ std::string check_sample(const rlbm_sample& s) {
 }
 
 }  // namespace
+
+// Message for rlbm_last_error(NULL) from entry points without a context.
+void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 }  // namespace rlbm
 
 using namespace rlbm;

@@ -65,6 +65,8 @@ EXPORTS = {
     "rlbm_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
     "rlbm_destroy": (None, [ctypes.c_void_p]),
     "rlbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "rlbm_velocity_residual_static": (ctypes.c_int, [ctypes.c_void_p] * 4 + [
+        ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
