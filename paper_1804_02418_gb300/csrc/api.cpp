@@ -248,7 +248,8 @@ int upload_ghosts(rlbm_ctx* c) {
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "ghost readback");
       for (int q = 0; q < kQ; ++q) {
-        const double v = patch[(size_t)q * kP * kP];
+        // site 0 of direction plane q / 4, shell q % 4 (four shells per site vector)
+        const double v = patch[(size_t)(q >> 2) * kP * kP * 4 + (q & 3)];
         c->samples[i].ghost[k][q] = v;
         ghost[(i * kMaxContacts + k) * kQ + q] = v;
       }

@@ -1,15 +1,18 @@
 // Kernels of the fused relativistic LBM step, templated on the storage type.
 //
-// Layout in HBM (per sample): two ping-pong buffers of 48 population planes
-// (structure of arrays), plane q holding the stored post-collision value of
-// population q for every site, row-major with row pitch ldx (a multiple of
-// 32 elements) and plane stride `plane` (a multiple of 64 elements).
+// Layout in HBM (per sample): two ping-pong buffers, each 12 direction planes
+// of `plane` sites (row-major, row pitch ldx a multiple of 32, plane a
+// multiple of 64 sites).  A site of direction plane d holds the four shells of
+// direction d side by side:
+//     element (d, site, j) = buffer[(d * plane + site) * 4 + j].
+// The four shells share their pull offset n_d, so one aligned vector access
+// moves them (the shift by n_d keeps the 16 / 32 / 8-byte alignment because
+// it moves by whole sites).
 //
-// One thread updates one site.  Pull scheme: the thread gathers the 48
-// post-collision populations arriving at its site (each warp reads 32
-// consecutive sites of a shifted row, so every load is coalesced), applies the
-// boundary rules, collides in registers and writes its own 48 values into the
-// other buffer (aligned, coalesced stores).
+// One thread updates one site.  Pull scheme: the thread gathers the 12 vectors
+// arriving at its site (each warp reads 32 consecutive sites of a shifted row:
+// coalesced), applies the boundary rules, collides in registers and writes 12
+// vectors of its own site into the other buffer.
 #pragma once
 #include "site.cuh"
 
@@ -23,6 +26,10 @@ struct StepAux {
   double* acc;           // [2] residual accumulators (sum |du|^2, sum |u|^2)
   unsigned* err;         // device error word
 };
+
+__device__ __forceinline__ long long vec_index(const DevSample& s, int d, long long site) {
+  return ((long long)d * s.plane + site) * 4;
+}
 
 // Index of the contact whose ghost strip holds the (outside) source (sx, sy).
 __device__ __forceinline__ int contact_of(const DevSample& s, int sx, int sy) {
@@ -42,26 +49,21 @@ template <typename S, bool INTERIOR, class C>
 __device__ __forceinline__ void pull(const S* __restrict__ fin, const DevSample& s, int x, int y,
                                      const typename Codec<S>::R* __restrict__ ghost, const C& qc,
                                      typename Codec<S>::R (&f)[kQ]) {
-  using R = typename Codec<S>::R;
   const long long site = (long long)y * s.ldx + x;
 #pragma unroll
   for (int d = 0; d < kDirs; ++d) {
     const int dx = hop_x(d), dy = hop_y(d);
     if (INTERIOR) {
-      const S* src = fin + (site - ((long long)dy * s.ldx + dx));
-#pragma unroll
-      for (int j = 0; j < kShells; ++j)
-        f[4 * d + j] = Codec<S>::load(__ldg(src + (long long)(4 * d + j) * s.plane), 4 * d + j, qc);
+      Codec<S>::load4(fin + vec_index(s, d, site - ((long long)dy * s.ldx + dx)), dir_kind(d),
+                      qc, &f[4 * d]);
     } else {
       int sx = x - dx, sy = y - dy;
       if (s.periodic_x) sx = sx < 0 ? sx + s.nx : (sx >= s.nx ? sx - s.nx : sx);
       if (s.periodic_y) sy = sy < 0 ? sy + s.ny : (sy >= s.ny ? sy - s.ny : sy);
       const bool inside = (unsigned)sx < (unsigned)s.nx && (unsigned)sy < (unsigned)s.ny;
       if (inside) {
-        const S* src = fin + ((long long)sy * s.ldx + sx);
-#pragma unroll
-        for (int j = 0; j < kShells; ++j)
-          f[4 * d + j] = Codec<S>::load(__ldg(src + (long long)(4 * d + j) * s.plane), 4 * d + j, qc);
+        Codec<S>::load4(fin + vec_index(s, d, (long long)sy * s.ldx + sx), dir_kind(d), qc,
+                        &f[4 * d]);
       } else {
         const int owner = contact_of(s, sx, sy);
         if (owner >= 0) {
@@ -69,11 +71,7 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, const DevSample&
           for (int j = 0; j < kShells; ++j) f[4 * d + j] = ghost[owner * kQ + 4 * d + j];
         } else {
           // bounce-back: post-collision population of the opposite direction, same shell
-          const S* src = fin + site;
-#pragma unroll
-          for (int j = 0; j < kShells; ++j)
-            f[4 * d + j] = Codec<S>::load(__ldg(src + (long long)(4 * (d ^ 1) + j) * s.plane),
-                                          4 * (d ^ 1) + j, qc);
+          Codec<S>::load4(fin + vec_index(s, d ^ 1, site), dir_kind(d), qc, &f[4 * d]);
         }
       }
     }
@@ -107,6 +105,31 @@ __device__ __forceinline__ void block_reduce_add2(double a, double b, double* ac
   }
 }
 
+// New deviations of the four shells of a direction from its cubic:
+// out_j = (1 - omega) f_j + w_j (R0 + R1 p0_j + R2 p0_j^2 + R3 p0_j^3).
+template <typename R, class C>
+__device__ __forceinline__ void relax_shells(const R (&Rm)[4], R omega, int kind, const C& qc,
+                                             R* f) {
+  const R omc = R(1) - omega;
+#pragma unroll
+  for (int j = 0; j < kShells; ++j) {
+    const R p = qc.p0[j];
+    const R val = fma(fma(fma(Rm[3], p, Rm[2]), p, Rm[1]), p, Rm[0]);
+    f[j] = fma(qc.w[kind][j], val, omc * f[j]);
+  }
+}
+
+// Adds sum_j (out_j - in_j) p0_j and sum_j (out_j - in_j) p0_j^2 of one direction.
+template <typename R, class C>
+__device__ __forceinline__ void balance(const R* in, const R* out, const C& qc, R& aN, R& aE) {
+#pragma unroll
+  for (int j = 0; j < kShells; ++j) {
+    const R dlt = out[j] - in[j];
+    aN = fma(dlt, qc.p0[j], aN);
+    aE = fma(dlt, qc.p0sq[j], aE);
+  }
+}
+
 // Fused stream + collide.  RES: 0 nothing extra; 1 store u for the residual;
 // 2 accumulate |u - u_prev|^2 and |u|^2.
 template <typename S, bool FORCE, int RES, class C>
@@ -115,6 +138,13 @@ __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restri
                                           const typename Codec<S>::R* __restrict__ ghost,
                                           const StepAux<typename Codec<S>::R>& aux, const C& qc) {
   using R = typename Codec<S>::R;
+  // FP32 storage: the FP32 quadrature constants satisfy Eq. orthonormal only
+  // to ~1e-7, which would break the exact conservation of N^0 and T^0a by the
+  // collision at that level every step (a secular drift).  The update is
+  // projected back onto the exact discrete balance
+  //   sum_i p0 (f* - f) = 0,  sum_i p0 p^a (f* - f) = (F.N_E, F N_E^0)
+  // by a correction on the (5,0)-type directions (solved with the constants P**, px).
+  constexpr bool kProject = sizeof(S) == sizeof(float);
   const int bx0 = blockIdx.x * kBX;
   const int x = bx0 + threadIdx.x;
   const int y = blockIdx.y;
@@ -122,7 +152,9 @@ __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restri
   double r_du2 = 0.0, r_u2 = 0.0;
   if (active) {
     R f[kQ];
-    const bool interior = bx0 >= kRadius && bx0 + kBX + kRadius <= s.nx &&
+    // warp-uniform: the 32 sites of this warp pull only from inside the rectangle
+    const int wx0 = x & ~31;
+    const bool interior = wx0 >= kRadius && wx0 + 32 + kRadius <= s.nx &&
                           y >= kRadius && y + kRadius < s.ny;
     if (interior) pull<S, true>(fin, s, x, y, ghost, qc, f);
     else          pull<S, false>(fin, s, x, y, ghost, qc, f);
@@ -137,48 +169,45 @@ __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restri
     if (bad) atomicOr(aux.err, bad);
 
     const EqCoeffs<R> c = eq_coeffs(M);
-    const R inv1T = R(1) / (R(1) + M.dT);
+    const R inv1T = qdiv(R(1), R(1) + M.dT);
     const R nT = (R(1) + M.dn) * inv1T;
     const R nmT = (M.dn - M.dT) * inv1T;
     const R gt = M.gamma * R(s.inv_tau);
+    const R gux = gt * M.ux, guy = gt * M.uy;
     const R Fx = R(s.Fx), Fy = R(s.Fy);
     const long long site = (long long)y * s.ldx + x;
-    // Reduced precision: the FP32 quadrature constants satisfy Eq. orthonormal
-    // only to ~1e-7, which would break the exact conservation of N^0 and T^0a
-    // by the collision at that level every step (a secular drift).  The
-    // update is therefore projected back onto the exact discrete balance
-    //   sum_i p0 (f* - f) = 0,  sum_i p0 p^a (f* - f) = (F.N_E, F N_E^0)
-    // with a correction w_i (l0 + l1 p0 + lx px + ly py); see below.
-    constexpr bool kProject = sizeof(R) < sizeof(double);
     R rN = R(0), rE = R(0), rX = R(0), rY = R(0);
+    // (5,0)-type pairs first: in reduced precision they take the correction
+    // and are stored last; the (3,4)-type pairs are stored as soon as done.
 #pragma unroll
-    for (int d = 0; d < kDirs; ++d) {
-      const R vx = R(hop_x(d)) / R(5), vy = R(hop_y(d)) / R(5);
-      const R omega = gt * (R(1) - vx * M.ux - vy * M.uy);
-      R Rm[4];
-      direction_cubic<R, FORCE>(d, c, nT, nmT, omega, Fx * vx + Fy * vy, Fy * vx - Fx * vy, Rm);
-      const R omc = R(1) - omega;
-      R aN = R(0), aE = R(0);
-#pragma unroll
-      for (int j = 0; j < kShells; ++j) {
-        const R p = qc.p0[j];
-        const R val = fma(fma(fma(Rm[3], p, Rm[2]), p, Rm[1]), p, Rm[0]);
-        const int q = 4 * d + j;
-        const R out = fma(qc.w[dir_kind(d)][j], val, omc * f[q]);
-        if (kProject) {
-          const R t = (out - f[q]) * p;
-          aN += t;
-          aE = fma(t, p, aE);
-          f[q] = out;
-        } else {
-          fout[(long long)q * s.plane + site] = Codec<S>::store(out, q, qc);
-        }
-      }
+    for (int pi = 0; pi < kDirs / 2; ++pi) {
+      const int d = (2 * pi + 8) % kDirs;
+      R Rp[4], Rn[4], omp, omn;
+      pair_cubics<R, FORCE>(d, c, nT, nmT, gt, gux, guy, Fx, Fy, Rp, Rn, omp, omn);
+      const int kind = dir_kind(d);
       if (kProject) {
-        rN += aN;
-        rE += aE;
-        if (hop_x(d) != 0) rX = fma(aE, vx, rX);
-        if (hop_y(d) != 0) rY = fma(aE, vy, rY);
+        R in[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) in[j] = f[4 * d + j];
+        relax_shells(Rp, omp, kind, qc, &f[4 * d]);
+        relax_shells(Rn, omn, kind, qc, &f[4 * d + 4]);
+        R aNp = R(0), aEp = R(0), aNn = R(0), aEn = R(0);
+        balance(in, &f[4 * d], qc, aNp, aEp);
+        balance(in + 4, &f[4 * d + 4], qc, aNn, aEn);
+        rN += aNp + aNn;
+        rE += aEp + aEn;
+        const R vx = R(hop_x(d)) / R(5), vy = R(hop_y(d)) / R(5);
+        if (hop_x(d) != 0) rX = fma(aEp - aEn, vx, rX);
+        if (hop_y(d) != 0) rY = fma(aEp - aEn, vy, rY);
+        if (kind == 0) {
+          Codec<S>::store4(fout + vec_index(s, d, site), kind, qc, &f[4 * d]);
+          Codec<S>::store4(fout + vec_index(s, d + 1, site), kind, qc, &f[4 * d + 4]);
+        }
+      } else {
+        relax_shells(Rp, omp, kind, qc, &f[4 * d]);
+        relax_shells(Rn, omn, kind, qc, &f[4 * d + 4]);
+        Codec<S>::store4(fout + vec_index(s, d, site), kind, qc, &f[4 * d]);
+        Codec<S>::store4(fout + vec_index(s, d + 1, site), kind, qc, &f[4 * d + 4]);
       }
     }
     if (kProject) {
@@ -189,21 +218,16 @@ __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restri
         rX -= nG * Fx;
         rY -= nG * Fy;
       }
-      // Solve with the exact shell moments sum_i w_i p0^K = K! (K = 1, 2, 3) and
-      // sum_i w_i p0^3 v_x^2 = 3: [1 2; 2 6] (l0, l1) = -(rN, rE), lx = -rX / 3.
-      const R l0 = R(-3) * rN + rE;
-      const R l1 = rN - R(0.5) * rE;
-      const R lx = rX * R(-1.0 / 3.0), ly = rY * R(-1.0 / 3.0);
+      const R l0 = qc.P00 * rN + qc.P01 * rE;
+      const R l1 = qc.P10 * rN + qc.P11 * rE;
+      const R lx = qc.px * rX, ly = qc.px * rY;
 #pragma unroll
-      for (int d = 0; d < kDirs; ++d) {
-        const R vx = R(hop_x(d)) / R(5), vy = R(hop_y(d)) / R(5);
-        const R cd = l1 + lx * vx + ly * vy;
+      for (int d = 8; d < kDirs; ++d) {
+        const R cd = l1 + (hop_x(d) > 0 ? lx : hop_x(d) < 0 ? -lx : hop_y(d) > 0 ? ly : -ly);
 #pragma unroll
-        for (int j = 0; j < kShells; ++j) {
-          const int q = 4 * d + j;
-          const R out = fma(qc.w[dir_kind(d)][j], fma(qc.p0[j], cd, l0), f[q]);
-          fout[(long long)q * s.plane + site] = Codec<S>::store(out, q, qc);
-        }
+        for (int j = 0; j < kShells; ++j)
+          f[4 * d + j] = fma(qc.w[1][j], fma(qc.p0[j], cd, l0), f[4 * d + j]);
+        Codec<S>::store4(fout + vec_index(s, d, site), 1, qc, &f[4 * d]);
       }
     }
     if (RES == 1) {
@@ -276,21 +300,21 @@ __device__ __forceinline__ void init_body(S* __restrict__ fout, const DevSample&
   const R nmT = (M.dn - M.dT) * inv1T;
   const long long site = (long long)y * s.ldx + x;
 #pragma unroll
-  for (int d = 0; d < kDirs; ++d) {
-    R Rm[4];
-    direction_cubic<R, false>(d, c, nT, nmT, R(1), R(0), R(0), Rm);
-#pragma unroll
-    for (int j = 0; j < kShells; ++j) {
-      const R p = qc.p0[j];
-      const R val = fma(fma(fma(Rm[3], p, Rm[2]), p, Rm[1]), p, Rm[0]);
-      const int q = 4 * d + j;
-      fout[(long long)q * s.plane + site] = Codec<S>::store(qc.w[dir_kind(d)][j] * val, q, qc);
-    }
+  for (int d = 0; d < kDirs; d += 2) {
+    R Rp[4], Rn[4], omp, omn;
+    // omega = 1 and no force: out = w (f^eq - w) / w
+    pair_cubics<R, false>(d, c, nT, nmT, R(1), R(0), R(0), R(0), R(0), Rp, Rn, omp, omn);
+    R v[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    relax_shells(Rp, R(1), dir_kind(d), qc, v);
+    relax_shells(Rn, R(1), dir_kind(d), qc, v + 4);
+    Codec<S>::store4(fout + vec_index(s, d, site), dir_kind(d), qc, v);
+    Codec<S>::store4(fout + vec_index(s, d + 1, site), dir_kind(d), qc, v + 4);
   }
 }
 
-// Dense FP64 deviations [48][ny][nx]  <->  stored planes.
-// Planes q0 .. q0 + gridDim.z - 1; `out` / `in` point at plane q0 of the dense array.
+// Dense FP64 deviations [48][ny][nx]  <->  stored vectors.
+// Populations q0 .. q0 + gridDim.z - 1; `out` / `in` point at population q0
+// of the dense array.
 template <typename S, class C>
 __device__ __forceinline__ void get_state_body(const S* __restrict__ fin, const DevSample& s,
                                                int q0, double* out, const C& qc) {
@@ -298,8 +322,9 @@ __device__ __forceinline__ void get_state_body(const S* __restrict__ fin, const 
   const int y = blockIdx.y;
   const int dq = blockIdx.z, q = q0 + dq;
   if (x >= s.nx) return;
-  const S v = fin[(long long)q * s.plane + (long long)y * s.ldx + x];
-  out[((long long)dq * s.ny + y) * s.nx + x] = double(Codec<S>::load(v, q, qc));
+  const int d = q >> 2, j = q & 3;
+  const S v = fin[vec_index(s, d, (long long)y * s.ldx + x) + j];
+  out[((long long)dq * s.ny + y) * s.nx + x] = double(Codec<S>::decode(v, dir_kind(d), j, qc));
 }
 
 template <typename S, class C>
@@ -310,8 +335,10 @@ __device__ __forceinline__ void set_state_body(S* __restrict__ fout, const DevSa
   const int y = blockIdx.y;
   const int dq = blockIdx.z, q = q0 + dq;
   if (x >= s.nx) return;
+  const int d = q >> 2, j = q & 3;
   const double v = in[((long long)dq * s.ny + y) * s.nx + x];
-  fout[(long long)q * s.plane + (long long)y * s.ldx + x] = Codec<S>::store(R(v), q, qc);
+  fout[vec_index(s, d, (long long)y * s.ldx + x) + j] =
+      Codec<S>::encode(R(v), dir_kind(d), j, qc);
 }
 
 }  // namespace rlbm

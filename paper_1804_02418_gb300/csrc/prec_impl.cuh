@@ -4,6 +4,8 @@
 #include "kernels.cuh"
 #include "ops.h"
 
+#include <cmath>
+
 namespace rlbm {
 namespace {
 
@@ -12,8 +14,15 @@ using R = typename Codec<S>::R;
 
 __constant__ QuadConsts<R> c_qc;
 
+#ifndef RLBM_STEP_MIN_BLOCKS
+#define RLBM_STEP_MIN_BLOCKS 1
+#endif
+
+// RLBM_STEP_MIN_BLOCKS: resident blocks per SM the register allocation aims
+// for (measured per storage type: FP32 runs best unconstrained at 128
+// registers, 16-bit storage at 5 blocks).
 template <bool FORCE, int RES>
-__global__ void __launch_bounds__(kBX) k_step(const S* __restrict__ fin, S* __restrict__ fout,
+__global__ void __launch_bounds__(kBX, RLBM_STEP_MIN_BLOCKS) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                               DevSample s, const R* __restrict__ ghost,
                                               StepAux<R> aux) {
   step_body<S, FORCE, RES>(fin, fout, s, ghost, aux, c_qc);
@@ -46,14 +55,25 @@ dim3 site_grid(const DevSample& s) { return dim3((s.nx + kBX - 1) / kBX, s.ny, 1
 
 cudaError_t upload(const double p0[4], const double w[2][4], double scale) {
   QuadConsts<R> h;
+  double K[4] = {0.0, 0.0, 0.0, 0.0};     // K_m = sum_j w_2j p0_j^m
   for (int j = 0; j < kShells; ++j) {
     h.p0[j] = R(p0[j]);
+    h.p0sq[j] = R(p0[j] * p0[j]);
     for (int k = 0; k < 2; ++k) {
       h.w[k][j] = R(w[k][j]);
       h.dec[k][j] = R(w[k][j] / scale);
       h.enc[k][j] = R(scale / w[k][j]);
     }
+    for (int m = 1; m <= 3; ++m) K[m] += w[1][j] * std::pow(p0[j], m);
   }
+  // Conservation projection on the four (5,0)-type directions:
+  //   [4K1 4K2; 4K2 4K3] (l0, l1) = -(rN, rE),   2 K3 lx = -rX,  2 K3 ly = -rY.
+  const double det = 16.0 * (K[1] * K[3] - K[2] * K[2]);
+  h.P00 = R(-4.0 * K[3] / det);
+  h.P01 = R(4.0 * K[2] / det);
+  h.P10 = R(4.0 * K[2] / det);
+  h.P11 = R(-4.0 * K[1] / det);
+  h.px = R(-1.0 / (2.0 * K[3]));
   return cudaMemcpyToSymbol(c_qc, &h, sizeof(h));
 }
 

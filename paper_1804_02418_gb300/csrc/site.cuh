@@ -42,9 +42,14 @@ __host__ __device__ constexpr int dir_kind(int d) { return d < 8 ? 0 : 1; }
 template <typename R>
 struct QuadConsts {
   R p0[kShells];            // shell energies p0_j
+  R p0sq[kShells];          // p0_j^2
   R w[2][kShells];          // weights by direction kind and shell
   R dec[2][kShells];        // 16-bit storage: delta = g * dec  (dec = w / s)
   R enc[2][kShells];        // 16-bit storage: g = delta * enc  (enc = s / w)
+  // Conservation projection (reduced precision): correction
+  // w_2j (l0 + l1 p0_j + p0_j (lx vx + ly vy)) on the (5,0)-type directions,
+  // (l0, l1) = P (rN, rE), (lx, ly) = px (rX, rY).
+  R P00, P01, P10, P11, px;
 };
 
 // Geometry and physics of one sample as seen by the kernels.
@@ -65,37 +70,76 @@ constexpr unsigned kErrUnphysical = 2u;
 constexpr unsigned kErrNoConvergence = 4u;
 
 // ---------------------------------------------------------------------------
-// Storage codecs: the stored value of population q and its deviation delta.
+// Storage codecs.  The four shells of one (direction, site) are stored side by
+// side, so one aligned vector access moves them (16 B for FP32, 32 B for FP64,
+// 8 B for 16-bit storage).  `kind` selects the weight row (0: (3,4)-type,
+// 1: (5,0)-type) for the 16-bit scaled relative deviations.
 // ---------------------------------------------------------------------------
 template <typename S> struct Codec;
 template <> struct Codec<double> {
   using R = double;
-  template <class C> __device__ static R load(double v, int, const C&) { return v; }
-  template <class C> __device__ static double store(R v, int, const C&) { return v; }
+  template <class C>
+  __device__ static void load4(const double* p, int, const C&, R* o) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  template <class C>
+  __device__ static void store4(double* p, int, const C&, const R* v) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+  template <class C> __device__ static R decode(double v, int, int, const C&) { return v; }
+  template <class C> __device__ static double encode(R v, int, int, const C&) { return v; }
 };
 template <> struct Codec<float> {
   using R = float;
-  template <class C> __device__ static R load(float v, int, const C&) { return v; }
-  template <class C> __device__ static float store(R v, int, const C&) { return v; }
+  template <class C>
+  __device__ static void load4(const float* p, int, const C&, R* o) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  }
+  template <class C>
+  __device__ static void store4(float* p, int, const C&, const R* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  template <class C> __device__ static R decode(float v, int, int, const C&) { return v; }
+  template <class C> __device__ static float encode(R v, int, int, const C&) { return v; }
 };
-template <> struct Codec<__half> {
+template <typename H> struct Codec16 {
   using R = float;
-  template <class C> __device__ static R load(__half v, int q, const C& c) {
-    return __half2float(v) * c.dec[dir_kind(q >> 2)][q & 3];
+  __device__ static float tof(H h);
+  __device__ static H fromf(float f);
+  template <class C>
+  __device__ static void load4(const H* p, int kind, const C& c, R* o) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    H h[4];
+    memcpy(h, &u, sizeof u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]) * c.dec[kind][j];
   }
-  template <class C> __device__ static __half store(R v, int q, const C& c) {
-    return __float2half_rn(v * c.enc[dir_kind(q >> 2)][q & 3]);
+  template <class C>
+  __device__ static void store4(H* p, int kind, const C& c, const R* v) {
+    H h[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = fromf(v[j] * c.enc[kind][j]);
+    uint2 u;
+    memcpy(&u, h, sizeof u);
+    *reinterpret_cast<uint2*>(p) = u;
+  }
+  template <class C> __device__ static R decode(H v, int kind, int j, const C& c) {
+    return tof(v) * c.dec[kind][j];
+  }
+  template <class C> __device__ static H encode(R v, int kind, int j, const C& c) {
+    return fromf(v * c.enc[kind][j]);
   }
 };
-template <> struct Codec<__nv_bfloat16> {
-  using R = float;
-  template <class C> __device__ static R load(__nv_bfloat16 v, int q, const C& c) {
-    return __bfloat162float(v) * c.dec[dir_kind(q >> 2)][q & 3];
-  }
-  template <class C> __device__ static __nv_bfloat16 store(R v, int q, const C& c) {
-    return __float2bfloat16_rn(v * c.enc[dir_kind(q >> 2)][q & 3]);
-  }
-};
+template <> __device__ inline float Codec16<__half>::tof(__half h) { return __half2float(h); }
+template <> __device__ inline __half Codec16<__half>::fromf(float f) { return __float2half_rn(f); }
+template <> __device__ inline float Codec16<__nv_bfloat16>::tof(__nv_bfloat16 h) { return __bfloat162float(h); }
+template <> __device__ inline __nv_bfloat16 Codec16<__nv_bfloat16>::fromf(float f) { return __float2bfloat16_rn(f); }
+template <> struct Codec<__half> : Codec16<__half> {};
+template <> struct Codec<__nv_bfloat16> : Codec16<__nv_bfloat16> {};
 
 // ---------------------------------------------------------------------------
 // Macroscopic state of one site (deviation form).
@@ -108,9 +152,13 @@ struct Macro {
   R deps;         // eps - 2
 };
 
-template <typename R> __device__ __forceinline__ R rsqrt_(R x);
-template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
-template <> __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+// Quotient and square root: correctly rounded in FP64; in FP32 the fast
+// hardware approximations (a few ulp), whose error is far below the FP32
+// storage rounding the arithmetic feeds.
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float qsqrt(float a) { return a * rsqrtf(a); }
 
 template <typename R> struct Tol;
 template <> struct Tol<double> { static constexpr double v = 1e-15; };
@@ -128,27 +176,30 @@ __device__ __forceinline__ Moments<R> moments(const R (&f)[kQ], const C& qc) {
   Moments<R> m;
   m.dN0 = m.dNx = m.dNy = m.dE = m.Mx = m.My = m.dPxx = m.dPxy = R(0);
 #pragma unroll
-  for (int d = 0; d < kDirs; ++d) {
-    // A_d = sum_j delta_dj p0_j ; B_d = sum_j delta_dj p0_j^2
-    R A = R(0), B = R(0);
+  for (int d = 0; d < kDirs; d += 2) {
+    // directions d and d + 1 are opposite: v_{d+1} = -v_d
+    R Ap = R(0), Bp = R(0), An = R(0), Bn = R(0);
 #pragma unroll
     for (int j = 0; j < kShells; ++j) {
-      const R t = f[4 * d + j] * qc.p0[j];
-      A += t;
-      B = fma(t, qc.p0[j], B);
+      Ap = fma(f[4 * d + j], qc.p0[j], Ap);
+      Bp = fma(f[4 * d + j], qc.p0sq[j], Bp);
+      An = fma(f[4 * d + 4 + j], qc.p0[j], An);
+      Bn = fma(f[4 * d + 4 + j], qc.p0sq[j], Bn);
     }
     const R vx = R(hop_x(d)) / R(5), vy = R(hop_y(d)) / R(5);
-    m.dN0 += A;
-    if (hop_x(d) != 0) m.dNx = fma(A, vx, m.dNx);
-    if (hop_y(d) != 0) m.dNy = fma(A, vy, m.dNy);
-    m.dE += B;
+    const R Ae = Ap + An, Ao = Ap - An, Be = Bp + Bn, Bo = Bp - Bn;
+    m.dN0 += Ae;
+    m.dE += Be;
     if (hop_x(d) != 0) {
-      const R Bx = B * vx;
-      m.Mx += Bx;
-      m.dPxx = fma(Bx, vx, m.dPxx);
-      if (hop_y(d) != 0) m.dPxy = fma(Bx, vy, m.dPxy);
+      m.dNx = fma(Ao, vx, m.dNx);
+      m.Mx = fma(Bo, vx, m.Mx);
+      m.dPxx = fma(Be, vx * vx, m.dPxx);
+      if (hop_y(d) != 0) m.dPxy = fma(Be, vx * vy, m.dPxy);
     }
-    if (hop_y(d) != 0) m.My = fma(B, vy, m.My);
+    if (hop_y(d) != 0) {
+      m.dNy = fma(Ao, vy, m.dNy);
+      m.My = fma(Bo, vy, m.My);
+    }
   }
   m.dPyy = m.dE - m.dPxx;   // massless shells: T^00 = T^xx + T^yy exactly
   return m;
@@ -165,27 +216,27 @@ __device__ __forceinline__ bool landau(const Moments<R>& m, Macro<R>& o) {
 #pragma unroll 1
   for (int it = 0; it < 12; ++it) {
     const R a = R(3) + m.dPxx + deps, c = R(3) + m.dPyy + deps;
-    const R inv = R(1) / (a * c - m.dPxy * m.dPxy);
+    const R inv = qdiv(R(1), a * c - m.dPxy * m.dPxy);
     ux = (c * m.Mx - m.dPxy * m.My) * inv;
     uy = (a * m.My - m.dPxy * m.Mx) * inv;
     const R g = deps - m.dE + m.Mx * ux + m.My * uy;
-    const R step = g / (R(1) - ux * ux - uy * uy);
+    const R step = qdiv(g, R(1) - ux * ux - uy * uy);
     deps -= step;
     if (fabs(step) <= Tol<R>::v * (R(2) + fabs(deps))) { conv = true; break; }
   }
   {
     const R a = R(3) + m.dPxx + deps, c = R(3) + m.dPyy + deps;
-    const R inv = R(1) / (a * c - m.dPxy * m.dPxy);
+    const R inv = qdiv(R(1), a * c - m.dPxy * m.dPxy);
     ux = (c * m.Mx - m.dPxy * m.My) * inv;
     uy = (a * m.My - m.dPxy * m.Mx) * inv;
   }
   const R u2 = ux * ux + uy * uy;
-  const R s = sqrt(R(1) - u2);
-  const R gamma = R(1) / s;
-  const R gm1 = u2 * gamma / (R(1) + s);
+  const R s = qsqrt(R(1) - u2);
+  const R gamma = qdiv(R(1), s);
+  const R gm1 = qdiv(u2 * gamma, R(1) + s);
   const R dNpar = m.dN0 - ux * m.dNx - uy * m.dNy;     // U_a N^a / gamma - 1
   const R dn = gm1 * (R(1) + dNpar) + dNpar;           // n - 1
-  const R dT = (deps - R(2) * dn) / (R(2) * (R(1) + dn));  // T - 1 = eps/(2n) - 1
+  const R dT = qdiv(deps - R(2) * dn, R(2) * (R(1) + dn));  // T - 1 = eps/(2n) - 1
   o.ux = ux; o.uy = uy; o.gamma = gamma; o.gm1 = gm1; o.dn = dn; o.dT = dT; o.deps = deps;
   return conv;
 }
@@ -242,18 +293,23 @@ __device__ __forceinline__ EqCoeffs<R> eq_coeffs(const Macro<R>& M) {
   c.c1_0 = a10 - R(2) * a200 + R(3) * a3000;
   c.c1_x = a1x - s3 * a20x + R(1.5) * a3xxx + R(0.5) * s15 * a300x;
   c.c1_y = a1y - s3 * a20y + s6 * a300y;
-  c.c2_0 = R(0.5) * a200 - a2xx / (R(2) * s3) - R(1.5) * a3000 + R(0.5) * s53 * a30xx;
-  c.c2_x = a20x / s3 - a3xxx - s53 * a300x;
-  c.c2_y = a20y / s3 - R(2) * s23 * a300y;
-  c.c2_xx = a2xx / s3 - s53 * a30xx;
-  c.c2_xy = a2xy / s3 - s53 * a30xy;
-  c.c3_0 = a3000 / R(6) - a30xx / (R(2) * s15);
-  c.c3_x = a300x / s15;
-  c.c3_y = a300y / (R(2) * s6) - a3xxy / (R(6) * s10);
-  c.c3_xx = a30xx / s15;
-  c.c3_xy = a30xy / s15;
-  c.c3_xxx = a3xxx / R(6) - a300x / (R(2) * s15);
-  c.c3_xxy = s25 / R(3) * a3xxy;
+  // reciprocals of the App. A normalisations (multiplications, not divisions)
+  const R i_s3 = R(0.57735026918962576), i_2s3 = R(0.28867513459481288);
+  const R i_s15 = R(0.25819888974716112), i_2s15 = R(0.12909944487358056);
+  const R i_2s6 = R(0.20412414523193151), i_6s10 = R(0.052704627669472988);
+  const R i_6 = R(1.0 / 6.0), s25_3 = R(0.21081851067789195);
+  c.c2_0 = R(0.5) * a200 - a2xx * i_2s3 - R(1.5) * a3000 + R(0.5) * s53 * a30xx;
+  c.c2_x = a20x * i_s3 - a3xxx - s53 * a300x;
+  c.c2_y = a20y * i_s3 - R(2) * s23 * a300y;
+  c.c2_xx = a2xx * i_s3 - s53 * a30xx;
+  c.c2_xy = a2xy * i_s3 - s53 * a30xy;
+  c.c3_0 = a3000 * i_6 - a30xx * i_2s15;
+  c.c3_x = a300x * i_s15;
+  c.c3_y = a300y * i_2s6 - a3xxy * i_6s10;
+  c.c3_xx = a30xx * i_s15;
+  c.c3_xy = a30xy * i_s15;
+  c.c3_xxx = a3xxx * i_6 - a300x * i_2s15;
+  c.c3_xxy = s25_3 * a3xxy;
   return c;
 }
 
@@ -264,36 +320,58 @@ __device__ __forceinline__ EqCoeffs<R> eq_coeffs(const Macro<R>& M) {
 // Forcing (force F per particle, dt = 1):
 //   F^ext / w = (n/T) [ (F.v) Q - F.grad Q ]  at p = p0 (1, v),
 // where grad is the gradient along the shell; with Q = sum_m p0^m q_m(theta)
-//   F.grad Q = sum_m p0^(m-1) [ m q_m (F.v) + dq_m/dtheta (F.t) ],  t = (-vy, vx).
+//   F.grad Q = sum_m p0^(m-1) [ m q_m (F.v) + dq_m/dtheta (F.t) ],  t = (-vy, vx),
+// so the p0^m coefficient of the source is
+//   s_m = (F.v) (q_m - (m+1) q_{m+1}) - (F.t) dq_{m+1}/dtheta.
+// Directions d (even) and d + 1 have opposite velocities; every polynomial is
+// split into its even and odd parts in v, evaluated once for the pair.
+// gux = gamma u_x / tau, guy = gamma u_y / tau, gt = gamma / tau.
 template <typename R, bool FORCE>
-__device__ __forceinline__ void direction_cubic(const int d, const EqCoeffs<R>& c, R nT, R nmT,
-                                                R omega, R Fv, R Ft, R (&Rm)[4]) {
+__device__ __forceinline__ void pair_cubics(const int d, const EqCoeffs<R>& c, R nT, R nmT,
+                                            R gt, R gux, R guy, R Fx, R Fy,
+                                            R (&Rp)[4], R (&Rn)[4], R& omp, R& omn) {
   const R vx = R(hop_x(d)) / R(5), vy = R(hop_y(d)) / R(5);
-  const R q1 = c.c1_0 + c.c1_x * vx + c.c1_y * vy;
-  const R q2 = c.c2_0 + c.c2_x * vx + c.c2_y * vy + c.c2_xx * (vx * vx) + c.c2_xy * (vx * vy);
-  const R q3 = c.c3_0 + c.c3_x * vx + c.c3_y * vy + c.c3_xx * (vx * vx) + c.c3_xy * (vx * vy)
-             + c.c3_xxx * (vx * vx * vx) + c.c3_xxy * (vx * vx * vy);
-  const R on = omega * nT;
-  Rm[0] = fma(omega, nmT, on * c.q0m1);
-  Rm[1] = on * q1;
-  Rm[2] = on * q2;
-  Rm[3] = on * q3;
+  R ow = R(0);
+  if (hop_x(d) != 0) ow = gux * vx;
+  if (hop_y(d) != 0) ow = fma(guy, vy, ow);
+  omp = gt - ow;
+  omn = gt + ow;
+  const R E2 = c.c2_0 + c.c2_xx * (vx * vx) + c.c2_xy * (vx * vy);
+  const R E3 = c.c3_0 + c.c3_xx * (vx * vx) + c.c3_xy * (vx * vy);
+  const R O1 = c.c1_x * vx + c.c1_y * vy;
+  const R O2 = c.c2_x * vx + c.c2_y * vy;
+  const R O3 = c.c3_x * vx + c.c3_y * vy + c.c3_xxx * (vx * vx * vx) + c.c3_xxy * (vx * vx * vy);
+  const R q1p = c.c1_0 + O1, q1n = c.c1_0 - O1;
+  const R q2p = E2 + O2, q2n = E2 - O2;
+  const R q3p = E3 + O3, q3n = E3 - O3;
+  const R onp = omp * nT, onn = omn * nT;
+  Rp[0] = fma(omp, nmT, onp * c.q0m1);
+  Rn[0] = fma(omn, nmT, onn * c.q0m1);
+  Rp[1] = onp * q1p;
+  Rn[1] = onn * q1n;
+  Rp[2] = onp * q2p;
+  Rn[2] = onn * q2n;
+  Rp[3] = onp * q3p;
+  Rn[3] = onn * q3n;
   if (FORCE) {
-    // dq_m/dtheta = -vy dq/dvx + vx dq/dvy
-    const R t1 = -vy * c.c1_x + vx * c.c1_y;
-    const R t2 = -vy * (c.c2_x + R(2) * vx * c.c2_xx + vy * c.c2_xy) + vx * (c.c2_y + vx * c.c2_xy);
-    const R t3 = -vy * (c.c3_x + R(2) * vx * c.c3_xx + vy * c.c3_xy + R(3) * (vx * vx) * c.c3_xxx
-                        + R(2) * (vx * vy) * c.c3_xxy)
-               + vx * (c.c3_y + vx * c.c3_xy + (vx * vx) * c.c3_xxy);
+    // F.v and F.t flip sign between the two directions; dq_m/dtheta = Et_m +- Ot_m
+    const R Fv = Fx * vx + Fy * vy, Ft = Fy * vx - Fx * vy;
+    const R Ot1 = -vy * c.c1_x + vx * c.c1_y;
+    const R Ot2 = -vy * c.c2_x + vx * c.c2_y;
+    const R Et2 = R(-2) * (vx * vy) * c.c2_xx + (vx * vx - vy * vy) * c.c2_xy;
+    const R Ot3 = -vy * c.c3_x + vx * c.c3_y - R(3) * (vx * vx * vy) * c.c3_xxx
+                + (vx * vx * vx - R(2) * vx * vy * vy) * c.c3_xxy;
+    const R Et3 = R(-2) * (vx * vy) * c.c3_xx + (vx * vx - vy * vy) * c.c3_xy;
     const R q0 = R(1) + c.q0m1;
-    const R s0 = Fv * (q0 - q1) - Ft * t1;
-    const R s1 = Fv * (q1 - R(2) * q2) - Ft * t2;
-    const R s2 = Fv * (q2 - R(3) * q3) - Ft * t3;
-    const R s3 = Fv * q3;
-    Rm[0] = fma(nT, s0, Rm[0]);
-    Rm[1] = fma(nT, s1, Rm[1]);
-    Rm[2] = fma(nT, s2, Rm[2]);
-    Rm[3] = fma(nT, s3, Rm[3]);
+    const R FvT = Fv * nT, FtT = Ft * nT;
+    Rp[0] = fma(FvT, q0 - q1p, fma(-FtT, Ot1, Rp[0]));
+    Rn[0] = fma(-FvT, q0 - q1n, fma(-FtT, Ot1, Rn[0]));
+    Rp[1] = fma(FvT, q1p - R(2) * q2p, fma(-FtT, Et2 + Ot2, Rp[1]));
+    Rn[1] = fma(-FvT, q1n - R(2) * q2n, fma(FtT, Et2 - Ot2, Rn[1]));
+    Rp[2] = fma(FvT, q2p - R(3) * q3p, fma(-FtT, Et3 + Ot3, Rp[2]));
+    Rn[2] = fma(-FvT, q2n - R(3) * q3n, fma(FtT, Et3 - Ot3, Rn[2]));
+    Rp[3] = fma(FvT, q3p, Rp[3]);
+    Rn[3] = fma(-FvT, q3n, Rn[3]);
   }
 }
 
