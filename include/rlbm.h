@@ -102,6 +102,11 @@ typedef struct {
                                    bytes, 256-byte aligned, borrowed (not freed);
                                    NULL: the context allocates its own */
   size_t workspace_bytes;
+  int graph_steps;              /* > 0 (even): rlbm_step replays CUDA graphs of this many
+                                   steps, captured on first use; needs a non-NULL
+                                   stream.  0: plain launches */
+  const char* tune_cache;       /* optional file where rlbm_autotune keeps its choices
+                                   (one line per GPU / precision / workload), or NULL */
 } rlbm_config;
 
 typedef struct rlbm_ctx rlbm_ctx;
@@ -129,6 +134,18 @@ int rlbm_init(rlbm_ctx* ctx, int sample, const double* n, const double* ux,
  * (RLBM_ENAN).  Needs nsteps >= 2 in that case.  Without residual the call
  * is asynchronous and checks nothing; use rlbm_check. */
 int rlbm_step(rlbm_ctx* ctx, int nsteps, double* residual);
+
+/* Residual of every sample, r_k = ||u_k(t) - u_k(t-1)|| / ||u_k(t)||, from the
+ * last rlbm_step call that asked for a residual (out holds nsamples values). */
+int rlbm_sample_residuals(const rlbm_ctx* ctx, double* out);
+
+/* Chooses the launch shape of the step kernel by timing the candidates on
+ * the current state (without advancing it): sites per block (64 / 128 / 256)
+ * and the number of blocks walking the work list of all samples (one per
+ * tile, or 1..16 per SM, persistent).  With rlbm_config.tune_cache the
+ * choice is read from / appended to that file.  Needs an initialised state.
+ * Writes the choice to *bx and *grid (may be NULL). */
+int rlbm_autotune(rlbm_ctx* ctx, int* bx, int* grid);
 
 /* Macroscopic fields (n, u_x, u_y, T) of `sample` at the current time: the
  * Landau-frame values of the streamed populations, i.e. those the next

@@ -114,8 +114,19 @@ struct rlbm_ctx {
   long long launches;
   size_t uprev_off, acc_off, err_off, ghost_off, stage_off;
   long long total_sites, max_sites;
-  double* host_pinned;        // 2 doubles + error word staging
+  double* host_pinned;        // residual accumulators + error word staging
   std::string err;
+  // launch shape: bx = 0 runs the single-sample kernel per sample; bx = 64 /
+  // 128 / 256 runs the batched kernel over all samples with `grid` blocks
+  int bx, grid;
+  int graph_steps;
+  std::string tune_cache;
+  cudaGraphExec_t graph[2];   // graph_steps steps starting from buffer 0 / 1
+  size_t dsamples_off, tiles_off[3];
+  long long ntiles[3];
+  bool force_any;
+  int sm_count;
+  std::vector<double> sample_res;
 };
 
 namespace {
@@ -158,6 +169,8 @@ size_t plan(const rlbm_config* cfg, const PrecOps* ops, rlbm_ctx* out) {
     d.ncontacts = s.ncontacts;
     d.plane = plane;
     d.site0 = total;
+    d.off[0] = (long long)(l.buf_off[0] / ops->elem_bytes);
+    d.off[1] = (long long)(l.buf_off[1] / ops->elem_bytes);
     d.inv_tau = 1.0 / s.tau;
     d.Fx = s.Fx; d.Fy = s.Fy;
     for (int k = 0; k < s.ncontacts; ++k) {
@@ -171,7 +184,14 @@ size_t plan(const rlbm_config* cfg, const PrecOps* ops, rlbm_ctx* out) {
   const size_t uprev_off = off;
   off = align_up(off + (size_t)total * 2 * ops->real_bytes, 256);
   const size_t acc_off = off;
-  off += 256;
+  off = align_up(off + (size_t)cfg->nsamples * 2 * sizeof(double), 256);
+  const size_t dsamples_off = off;
+  off = align_up(off + (size_t)cfg->nsamples * sizeof(DevSample), 256);
+  size_t tiles_off[3];
+  for (int b = 0; b < 3; ++b) {
+    tiles_off[b] = off;
+    off = align_up(off + (size_t)(cfg->nsamples + 1) * sizeof(long long), 256);
+  }
   const size_t err_off = off;
   off += 256;
   const size_t ghost_off = off;
@@ -185,6 +205,8 @@ size_t plan(const rlbm_config* cfg, const PrecOps* ops, rlbm_ctx* out) {
     out->samples = std::move(L);
     out->uprev_off = uprev_off;
     out->acc_off = acc_off;
+    out->dsamples_off = dsamples_off;
+    for (int b = 0; b < 3; ++b) out->tiles_off[b] = tiles_off[b];
     out->err_off = err_off;
     out->ghost_off = ghost_off;
     out->stage_off = stage_off;
@@ -278,6 +300,127 @@ const void* ghost_ptr(rlbm_ctx* c, int sample) {
   return c->ws + c->ghost_off + (size_t)sample * kMaxContacts * kQ * c->ops->real_bytes;
 }
 
+
+constexpr int kBxChoices[3] = {64, 128, 256};
+
+int bx_slot(int bx) { return bx == 64 ? 0 : bx == 256 ? 2 : 1; }
+
+// Device table of the samples and, per tile width, the first tile of every
+// sample (the work list of the batched kernel).
+int upload_tables(rlbm_ctx* c) {
+  const size_t n = c->samples.size();
+  std::vector<DevSample> ds(n);
+  for (size_t i = 0; i < n; ++i) ds[i] = c->samples[i].dev;
+  cudaError_t e = cudaMemcpyAsync(c->ws + c->dsamples_off, ds.data(), n * sizeof(DevSample),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sample table upload");
+  std::vector<long long> ts[3];
+  for (int b = 0; b < 3; ++b) {
+    ts[b].assign(n + 1, 0);
+    for (size_t i = 0; i < n; ++i) {
+      const DevSample& d = c->samples[i].dev;
+      ts[b][i + 1] = ts[b][i] + (long long)d.ny * ((d.nx + kBxChoices[b] - 1) / kBxChoices[b]);
+    }
+    c->ntiles[b] = ts[b][n];
+    e = cudaMemcpyAsync(c->ws + c->tiles_off[b], ts[b].data(), (n + 1) * sizeof(long long),
+                        cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tile list upload");
+  }
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  return RLBM_OK;
+}
+
+// Launches one time step reading buffer `from` (0 / 1) with the shape (bx, grid).
+cudaError_t launch_step(rlbm_ctx* c, int from, int res, int bx, int grid) {
+  double* acc = at<double>(c, c->acc_off);
+  unsigned* err = at<unsigned>(c, c->err_off);
+  void* uprev = c->ws + c->uprev_off;
+  if (bx == 0) {
+    for (size_t i = 0; i < c->samples.size(); ++i) {
+      SampleLayout& L = c->samples[i];
+      const bool force = L.desc.Fx != 0.0 || L.desc.Fy != 0.0;
+      cudaError_t e = c->ops->step(buf(c, (int)i, from), buf(c, (int)i, from ^ 1), L.dev,
+                                   ghost_ptr(c, (int)i), force, res, uprev, acc + 2 * i, err,
+                                   c->stream);
+      if (e != cudaSuccess) return e;
+      c->launches++;
+    }
+    return cudaSuccess;
+  }
+  const int b = bx_slot(bx);
+  BatchArgs a;
+  a.samples = reinterpret_cast<const DevSample*>(c->ws + c->dsamples_off);
+  a.tile_start = reinterpret_cast<const long long*>(c->ws + c->tiles_off[b]);
+  a.nsamples = (int)c->samples.size();
+  a.cur = from;
+  a.ntiles = c->ntiles[b];
+  const int g = grid > 0 ? grid : (int)std::min<long long>(a.ntiles, 1LL << 30);
+  cudaError_t e = c->ops->step_batch(c->ws, a, c->ws + c->ghost_off, c->force_any, res, bx, g,
+                                     uprev, acc, err, c->stream);
+  if (e == cudaSuccess) c->launches++;
+  return e;
+}
+
+// One time step of the context with its current shape; advances the parity.
+int advance(rlbm_ctx* c, int res) {
+  cudaError_t e = launch_step(c, c->cur, res, c->bx, c->grid);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+  c->cur ^= 1;
+  c->steps++;
+  return RLBM_OK;
+}
+
+void drop_graphs(rlbm_ctx* c) {
+  for (int k = 0; k < 2; ++k)
+    if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
+}
+
+// CUDA graph of graph_steps steps starting from buffer `parity`, captured once.
+int graph_for(rlbm_ctx* c, int parity, cudaGraphExec_t* out) {
+  if (c->graph[parity]) { *out = c->graph[parity]; return RLBM_OK; }
+  const int cur = c->cur;
+  const long long steps = c->steps, launches = c->launches;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+  c->cur = parity;
+  int r = RLBM_OK;
+  for (int k = 0; k < c->graph_steps && r == RLBM_OK; ++k) r = advance(c, 0);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->stream, &g);
+  c->cur = cur;
+  c->steps = steps;
+  c->launches = launches;
+  if (r) { if (g) cudaGraphDestroy(g); return r; }
+  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+  e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { c->graph[parity] = nullptr; return cuda_fail(c, e, "instantiate graph"); }
+  *out = c->graph[parity];
+  return RLBM_OK;
+}
+
+long long launches_per_step(const rlbm_ctx* c) {
+  return c->bx == 0 ? (long long)c->samples.size() : 1;
+}
+
+std::string tune_key(const rlbm_ctx* c) {
+  cudaDeviceProp p;
+  cudaGetDeviceProperties(&p, c->device);
+  unsigned long long h = 1469598103934665603ULL;   // FNV-1a over the geometry
+  auto mix = [&](long long v) { for (int k = 0; k < 8; ++k) { h ^= (v >> (8 * k)) & 255; h *= 1099511628211ULL; } };
+  for (auto& L : c->samples) {
+    mix(L.desc.nx); mix(L.desc.ny); mix(L.desc.periodic_x); mix(L.desc.periodic_y);
+    mix(L.desc.ncontacts);
+  }
+  char b[512];
+  std::string name = p.name;
+  for (auto& ch : name) if (ch == ' ') ch = '_';
+  snprintf(b, sizeof b, "%s|%s|n=%zu|sites=%lld|force=%d|h=%016llx", name.c_str(), c->ops->name,
+           c->samples.size(), c->total_sites, (int)c->force_any, h);
+  return b;
+}
+
 int check_sample_index(rlbm_ctx* c, int sample) {
   if (!c) return RLBM_EINVAL;
   if (sample < 0 || sample >= (int)c->samples.size())
@@ -323,7 +466,16 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out) {
   c->steps = 0;
   c->launches = 0;
   c->host_pinned = nullptr;
+  c->graph[0] = c->graph[1] = nullptr;
+  c->graph_steps = cfg->graph_steps > 0 ? cfg->graph_steps : 0;
+  if (c->graph_steps & 1) c->graph_steps += 1;          // even: a replay keeps the buffer parity
+  c->tune_cache = cfg->tune_cache ? cfg->tune_cache : "";
+  c->force_any = false;
+  for (int i = 0; i < cfg->nsamples; ++i)
+    c->force_any |= cfg->samples[i].Fx != 0.0 || cfg->samples[i].Fy != 0.0;
   cudaGetDevice(&c->device);
+  c->sm_count = 0;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
   const size_t need = plan(cfg, c->ops, c);
   c->sample_ready.assign(c->samples.size(), 0);
   if (cfg->workspace) {
@@ -345,7 +497,9 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out) {
     c->owns_workspace = true;
   }
   c->ws_bytes = need;
-  cudaError_t e = cudaMallocHost((void**)&c->host_pinned, 256);
+  c->sample_res.assign(c->samples.size(), 0.0);
+  cudaError_t e = cudaMallocHost((void**)&c->host_pinned,
+                                 (2 * c->samples.size() + 2) * sizeof(double));
   if (e != cudaSuccess) { rlbm_destroy(c); return fail(nullptr, RLBM_ENOMEM, "pinned staging"); }
   const double w[2][4] = {{q.w1[0], q.w1[1], q.w1[2], q.w1[3]}, {q.w2[0], q.w2[1], q.w2[2], q.w2[3]}};
   e = c->ops->upload(q.p0, w, storage_scale(c->prec));
@@ -356,6 +510,10 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out) {
   if (e != cudaSuccess) { rlbm_destroy(c); return fail(nullptr, RLBM_ECUDA, "memset: %s", cudaGetErrorString(e)); }
   r = upload_ghosts(c);
   if (r) { std::string m = c->err; rlbm_destroy(c); return fail(nullptr, r, "%s", m.c_str()); }
+  r = upload_tables(c);
+  if (r) { std::string m = c->err; rlbm_destroy(c); return fail(nullptr, r, "%s", m.c_str()); }
+  c->bx = c->samples.size() == 1 ? 0 : 128;
+  c->grid = c->samples.size() == 1 ? 0 : (int)std::min<long long>(c->ntiles[1], 1LL << 30);
   *out = c;
   return RLBM_OK;
 }
@@ -363,6 +521,8 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out) {
 void rlbm_destroy(rlbm_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  for (int k = 0; k < 2; ++k)
+    if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
   if (c->owns_workspace && c->ws) cudaFree(c->ws);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   delete c;
@@ -416,45 +576,138 @@ int rlbm_step(rlbm_ctx* c, int nsteps, double* residual) {
   if (nsteps < 0) return fail(c, RLBM_EINVAL, "nsteps < 0");
   if (!c->initialised) return fail(c, RLBM_ESTATE, "rlbm_init or rlbm_set_state first");
   if (residual && nsteps < 2) return fail(c, RLBM_EINVAL, "residual needs nsteps >= 2");
+  const size_t ns = c->samples.size();
   double* acc = at<double>(c, c->acc_off);
   unsigned* err = at<unsigned>(c, c->err_off);
-  void* uprev = c->ws + c->uprev_off;
   if (residual) {
-    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), c->stream);
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * ns * sizeof(double), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
   }
-  for (int t = 0; t < nsteps; ++t) {
-    int res = 0;
-    if (residual && t == nsteps - 2) res = 1;
-    if (residual && t == nsteps - 1) res = 2;
-    for (size_t i = 0; i < c->samples.size(); ++i) {
-      SampleLayout& L = c->samples[i];
-      const bool force = L.desc.Fx != 0.0 || L.desc.Fy != 0.0;
-      cudaError_t e = c->ops->step(buf(c, (int)i, c->cur), buf(c, (int)i, c->cur ^ 1), L.dev,
-                                   ghost_ptr(c, (int)i), force, res, uprev, acc, err, c->stream);
-      if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
-      c->launches++;
+  const int plain = nsteps - (residual ? 2 : 0);
+  int t = 0;
+  if (c->graph_steps > 0 && c->stream) {
+    while (plain - t >= c->graph_steps) {
+      cudaGraphExec_t g;
+      int r = graph_for(c, c->cur, &g);
+      if (r) return r;
+      cudaError_t e = cudaGraphLaunch(g, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+      c->steps += c->graph_steps;
+      c->launches += c->graph_steps * launches_per_step(c);
+      t += c->graph_steps;
     }
-    c->cur ^= 1;
-    c->steps++;
+  }
+  for (; t < plain; ++t) {
+    int r = advance(c, 0);
+    if (r) return r;
   }
   if (residual) {
-    cudaError_t e = cudaMemcpyAsync(c->host_pinned, acc, 2 * sizeof(double),
+    int r = advance(c, 1);
+    if (!r) r = advance(c, 2);
+    if (r) return r;
+    cudaError_t e = cudaMemcpyAsync(c->host_pinned, acc, 2 * ns * sizeof(double),
                                     cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->host_pinned + 2, err, sizeof(unsigned), cudaMemcpyDeviceToHost,
+      e = cudaMemcpyAsync(c->host_pinned + 2 * ns, err, sizeof(unsigned), cudaMemcpyDeviceToHost,
                           c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "residual readback");
-    const double num = c->host_pinned[0], den = c->host_pinned[1];
+    double num = 0.0, den = 0.0;
+    for (size_t i = 0; i < ns; ++i) {
+      const double a = c->host_pinned[2 * i], b = c->host_pinned[2 * i + 1];
+      c->sample_res[i] = b > 0 ? std::sqrt(a / b) : (a == 0 ? 0.0 : INFINITY);
+      num += a;
+      den += b;
+    }
     *residual = den > 0 ? std::sqrt(num / den) : (num == 0 ? 0.0 : INFINITY);
     unsigned bits;
-    std::memcpy(&bits, c->host_pinned + 2, sizeof bits);
+    std::memcpy(&bits, c->host_pinned + 2 * ns, sizeof bits);
     if (bits) {
       cudaMemsetAsync(err, 0, sizeof(unsigned), c->stream);
       return fail(c, RLBM_ENAN, "device error word 0x%x (1 non-finite, 2 unphysical, 4 no convergence)", bits);
     }
   }
+  return RLBM_OK;
+}
+
+int rlbm_sample_residuals(const rlbm_ctx* c, double* out) {
+  if (!c || !out) return RLBM_EINVAL;
+  for (size_t i = 0; i < c->sample_res.size(); ++i) out[i] = c->sample_res[i];
+  return RLBM_OK;
+}
+
+int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out) {
+  if (!c) return RLBM_EINVAL;
+  if (!c->initialised) return fail(c, RLBM_ESTATE, "rlbm_init or rlbm_set_state first");
+  const std::string key = tune_key(c);
+  bool found = false;
+  if (!c->tune_cache.empty()) {
+    if (FILE* f = fopen(c->tune_cache.c_str(), "r")) {
+      char line[768];
+      while (fgets(line, sizeof line, f)) {
+        char k[640];
+        int bx, grid;
+        if (sscanf(line, "%639s %d %d", k, &bx, &grid) == 3 && key == k &&
+            (bx == 0 || bx == 64 || bx == 128 || bx == 256) && grid >= 0) {
+          c->bx = bx;
+          c->grid = grid;
+          found = true;
+        }
+      }
+      fclose(f);
+    }
+  }
+  if (!found) {
+    struct Cand { int bx, grid; };
+    std::vector<Cand> cands;
+    if (c->samples.size() == 1) cands.push_back({0, 0});
+    for (int b = 0; b < 3; ++b) {
+      const int bx = kBxChoices[b];
+      cands.push_back({bx, 0});                       // one block per tile
+      for (int m : {1, 2, 4, 8, 16}) {
+        const long long g = (long long)m * c->sm_count * (256 / bx);
+        if (g < c->ntiles[b]) cands.push_back({bx, (int)g});
+      }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    Cand pick = {c->bx, c->grid};
+    const long long launches = c->launches;
+    for (const Cand& k : cands) {
+      // repeated steps from the same input buffer: the state does not advance
+      cudaError_t e = cudaSuccess;
+      for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_step(c, c->cur, 0, k.bx, k.grid);
+      cudaEventRecord(e0, c->stream);
+      const int reps = 5;
+      for (int w = 0; w < reps && e == cudaSuccess; ++w) e = launch_step(c, c->cur, 0, k.bx, k.grid);
+      cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(c, e, "autotune launch");
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; pick = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->launches = launches;
+    c->bx = pick.bx;
+    c->grid = pick.grid;
+    if (!c->tune_cache.empty()) {
+      if (FILE* f = fopen(c->tune_cache.c_str(), "a")) {
+        fprintf(f, "%s %d %d\n", key.c_str(), c->bx, c->grid);
+        fclose(f);
+      }
+    }
+  }
+  drop_graphs(c);
+  if (bx_out) *bx_out = c->bx;
+  if (grid_out) *grid_out = c->grid;
   return RLBM_OK;
 }
 

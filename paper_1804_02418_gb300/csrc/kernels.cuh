@@ -130,13 +130,16 @@ __device__ __forceinline__ void balance(const R* in, const R* out, const C& qc, 
   }
 }
 
-// Fused stream + collide.  RES: 0 nothing extra; 1 store u for the residual;
-// 2 accumulate |u - u_prev|^2 and |u|^2.
+// Fused stream + collide of site (x, y) (nothing if x >= nx).  RES: 0 nothing
+// extra; 1 store u for the residual; 2 add |u - u_prev|^2 and |u|^2 to
+// r_du2, r_u2 (the caller reduces them).  All 32 threads of a warp must hold
+// consecutive x of the same row (the interior test is per warp).
 template <typename S, bool FORCE, int RES, class C>
-__device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restrict__ fout,
-                                          const DevSample& s,
+__device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restrict__ fout,
+                                          const DevSample& s, int x, int y,
                                           const typename Codec<S>::R* __restrict__ ghost,
-                                          const StepAux<typename Codec<S>::R>& aux, const C& qc) {
+                                          const StepAux<typename Codec<S>::R>& aux, const C& qc,
+                                          double& r_du2, double& r_u2) {
   using R = typename Codec<S>::R;
   // FP32 storage: the FP32 quadrature constants satisfy Eq. orthonormal only
   // to ~1e-7, which would break the exact conservation of N^0 and T^0a by the
@@ -145,12 +148,7 @@ __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restri
   //   sum_i p0 (f* - f) = 0,  sum_i p0 p^a (f* - f) = (F.N_E, F N_E^0)
   // by a correction on the (5,0)-type directions (solved with the constants P**, px).
   constexpr bool kProject = sizeof(S) == sizeof(float);
-  const int bx0 = blockIdx.x * kBX;
-  const int x = bx0 + threadIdx.x;
-  const int y = blockIdx.y;
-  const bool active = x < s.nx;
-  double r_du2 = 0.0, r_u2 = 0.0;
-  if (active) {
+  if (x < s.nx) {
     R f[kQ];
     // warp-uniform: the 32 sites of this warp pull only from inside the rectangle
     const int wx0 = x & ~31;
@@ -238,11 +236,64 @@ __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restri
       const long long k = s.site0 + (long long)y * s.nx + x;
       const double dx = double(M.ux) - double(aux.uprev[2 * k]);
       const double dy = double(M.uy) - double(aux.uprev[2 * k + 1]);
-      r_du2 = dx * dx + dy * dy;
-      r_u2 = double(M.ux) * double(M.ux) + double(M.uy) * double(M.uy);
+      r_du2 += dx * dx + dy * dy;
+      r_u2 += double(M.ux) * double(M.ux) + double(M.uy) * double(M.uy);
     }
   }
-  if (RES == 2) block_reduce_add2<R>(r_du2, r_u2, aux.acc);
+}
+
+// One sample, one block row of kBX sites.
+template <typename S, bool FORCE, int RES, class C>
+__device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restrict__ fout,
+                                          const DevSample& s,
+                                          const typename Codec<S>::R* __restrict__ ghost,
+                                          const StepAux<typename Codec<S>::R>& aux, const C& qc) {
+  double r_du2 = 0.0, r_u2 = 0.0;
+  site_step<S, FORCE, RES>(fin, fout, s, blockIdx.x * kBX + threadIdx.x, blockIdx.y, ghost, aux,
+                           qc, r_du2, r_u2);
+  if (RES == 2) block_reduce_add2<typename Codec<S>::R>(r_du2, r_u2, aux.acc);
+}
+
+// Many samples of uneven size in one launch.  The work list is every row
+// segment of BX sites of every sample ("tile"), numbered sample by sample;
+// tile_start[k] is the first tile of sample k (tile_start[nsamples] = total).
+// Blocks walk the list with a grid stride (persistent when the grid is a
+// multiple of the SM count).  Sample k's buffers are base + samples[k].off[cur]
+// (input) and base + samples[k].off[1 - cur] (output).
+struct BatchArgs {
+  const DevSample* samples;
+  const long long* tile_start;
+  int nsamples;
+  int cur;
+  long long ntiles;
+};
+
+template <typename S, bool FORCE, int RES, int BX, class C>
+__device__ __forceinline__ void batch_body(S* __restrict__ base, const BatchArgs& b,
+                                           const typename Codec<S>::R* __restrict__ ghost,
+                                           const StepAux<typename Codec<S>::R>& aux, const C& qc) {
+  for (long long t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    int lo = 0, hi = b.nsamples;                 // tile_start[lo] <= t < tile_start[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(b.tile_start + mid) <= t) lo = mid; else hi = mid;
+    }
+    const DevSample s = b.samples[lo];
+    const long long lt = t - __ldg(b.tile_start + lo);
+    const int tpr = (s.nx + BX - 1) / BX;
+    const int y = (int)(lt / tpr);
+    const int x = (int)(lt - (long long)y * tpr) * BX + threadIdx.x;
+    const long long oin = b.cur ? s.off[1] : s.off[0];
+    const long long oout = b.cur ? s.off[0] : s.off[1];
+    double r_du2 = 0.0, r_u2 = 0.0;
+    site_step<S, FORCE, RES>(base + oin, base + oout, s, x, y,
+                             ghost + (long long)lo * kMaxContacts * kQ, aux, qc, r_du2, r_u2);
+    // per-sample residual accumulators: acc[2 k], acc[2 k + 1]
+    if (RES == 2) {
+      block_reduce_add2<typename Codec<S>::R>(r_du2, r_u2, aux.acc + 2 * lo);
+      __syncthreads();   // the reduction's shared scratch is reused by the next tile
+    }
+  }
 }
 
 // Macroscopic fields of the streamed populations (no collision).

@@ -2,7 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
-#include "site.cuh"
+#include "kernels.cuh"
 
 namespace rlbm {
 
@@ -15,6 +15,11 @@ struct PrecOps {
   cudaError_t (*step)(const void* fin, void* fout, const DevSample& s, const void* ghost,
                       bool force, int res, void* uprev, double* acc, unsigned* err,
                       cudaStream_t st);
+  // All samples in one launch over the tile list (bx: 64 / 128 / 256 sites per
+  // tile and block; grid: number of blocks walking the list).
+  cudaError_t (*step_batch)(void* base, const BatchArgs& b, const void* ghost, bool force,
+                            int res, int bx, int grid, void* uprev, double* acc,
+                            unsigned* err, cudaStream_t st);
   cudaError_t (*moments)(const void* fin, const DevSample& s, const void* ghost, double* n,
                          double* ux, double* uy, double* T, unsigned* err, cudaStream_t st);
   cudaError_t (*init)(void* fout, const DevSample& s, const double* n, const double* ux,

@@ -14,18 +14,24 @@ using R = typename Codec<S>::R;
 
 __constant__ QuadConsts<R> c_qc;
 
+// RLBM_STEP_MIN_BLOCKS: resident blocks per SM the register allocation aims
+// for (measured per storage type: FP32 runs best at 4 blocks / 128
+// registers, 16-bit storage at 5 blocks).
 #ifndef RLBM_STEP_MIN_BLOCKS
-#define RLBM_STEP_MIN_BLOCKS 1
+#define RLBM_STEP_MIN_BLOCKS 4
 #endif
 
-// RLBM_STEP_MIN_BLOCKS: resident blocks per SM the register allocation aims
-// for (measured per storage type: FP32 runs best unconstrained at 128
-// registers, 16-bit storage at 5 blocks).
 template <bool FORCE, int RES>
 __global__ void __launch_bounds__(kBX, RLBM_STEP_MIN_BLOCKS) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                               DevSample s, const R* __restrict__ ghost,
                                               StepAux<R> aux) {
   step_body<S, FORCE, RES>(fin, fout, s, ghost, aux, c_qc);
+}
+
+template <bool FORCE, int RES, int BX>
+__global__ void __launch_bounds__(BX, RLBM_STEP_MIN_BLOCKS * kBX / BX)
+k_step_batch(S* __restrict__ base, BatchArgs b, const R* __restrict__ ghost, StepAux<R> aux) {
+  batch_body<S, FORCE, RES, BX>(base, b, ghost, aux, c_qc);
 }
 
 __global__ void __launch_bounds__(kBX) k_moments(const S* __restrict__ fin, DevSample s,
@@ -96,6 +102,32 @@ cudaError_t step(const void* fin, void* fout, const DevSample& s, const void* gh
   return cudaGetLastError();
 }
 
+template <int BX>
+void launch_batch(S* base, const BatchArgs& b, const R* g, bool force, int res, int grid,
+                  const StepAux<R>& aux, cudaStream_t st) {
+  if (force) {
+    if (res == 0) k_step_batch<true, 0, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
+    else if (res == 1) k_step_batch<true, 1, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
+    else k_step_batch<true, 2, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
+  } else {
+    if (res == 0) k_step_batch<false, 0, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
+    else if (res == 1) k_step_batch<false, 1, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
+    else k_step_batch<false, 2, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
+  }
+}
+
+cudaError_t step_batch(void* base, const BatchArgs& b, const void* ghost, bool force, int res,
+                       int bx, int grid, void* uprev, double* acc, unsigned* err,
+                       cudaStream_t st) {
+  StepAux<R> aux{static_cast<R*>(uprev), acc, err};
+  S* p = static_cast<S*>(base);
+  const R* g = static_cast<const R*>(ghost);
+  if (bx == 64) launch_batch<64>(p, b, g, force, res, grid, aux, st);
+  else if (bx == 256) launch_batch<256>(p, b, g, force, res, grid, aux, st);
+  else launch_batch<128>(p, b, g, force, res, grid, aux, st);
+  return cudaGetLastError();
+}
+
 cudaError_t moments(const void* fin, const DevSample& s, const void* ghost, double* n, double* ux,
                     double* uy, double* T, unsigned* err, cudaStream_t st) {
   k_moments<<<site_grid(s), kBX, 0, st>>>(static_cast<const S*>(fin), s,
@@ -126,7 +158,8 @@ cudaError_t set_state(void* fout, const DevSample& s, int q0, int nq, const doub
 }
 
 const PrecOps kOps = {
-    RLBM_NAME, sizeof(S), sizeof(R), upload, step, moments, init, get_state, set_state, 1,
+    RLBM_NAME, sizeof(S), sizeof(R), upload, step, step_batch, moments, init, get_state,
+    set_state, 1,
 };
 
 }  // namespace

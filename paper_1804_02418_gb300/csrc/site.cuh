@@ -59,6 +59,7 @@ struct DevSample {
   int ncontacts;
   long long plane;                    // elements per population plane
   long long site0;                    // first site of this sample in the flat u / mask arrays
+  long long off[2];                   // element offsets of the two buffers (batched launches)
   double inv_tau;
   double Fx, Fy;
   int cedge[kMaxContacts], clo[kMaxContacts], chi[kMaxContacts];

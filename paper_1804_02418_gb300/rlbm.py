@@ -45,7 +45,8 @@ class _Sample(ctypes.Structure):
 class _Config(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("nsamples", ctypes.c_int),
                 ("samples", ctypes.POINTER(_Sample)), ("stream", ctypes.c_void_p),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("graph_steps", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
 
 
 _LIB = None
@@ -65,6 +66,9 @@ EXPORTS = {
     "rlbm_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
     "rlbm_destroy": (None, [ctypes.c_void_p]),
     "rlbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "rlbm_sample_residuals": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "rlbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
     "rlbm_velocity_residual_static": (ctypes.c_int, [ctypes.c_void_p] * 4 + [
         ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -131,7 +135,8 @@ def _ptr(a):
 class Solver:
     """A context advancing one or more samples together on the current CUDA device."""
 
-    def __init__(self, samples, prec: str = "f32", stream=None, workspace: Optional[str] = "torch"):
+    def __init__(self, samples, prec: str = "f32", stream=None, workspace: Optional[str] = "torch",
+                 graph_steps: int = 0, tune_cache: Optional[str] = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -147,6 +152,9 @@ class Solver:
         cfg.nsamples = len(self.samples)
         cfg.samples = self._csamples
         cfg.stream = ctypes.c_void_p(self._stream.cuda_stream)
+        cfg.graph_steps = int(graph_steps)
+        self._tune_cache = tune_cache.encode() if tune_cache else None
+        cfg.tune_cache = self._tune_cache
         need = ctypes.c_size_t()
         self._check(self.lib.rlbm_workspace_size(ctypes.byref(cfg), ctypes.byref(need)), None)
         self.workspace_bytes = need.value
@@ -228,6 +236,17 @@ class Solver:
 
     def check(self):
         self._check(self.lib.rlbm_check(self.ctx))
+
+    def sample_residuals(self):
+        out = (ctypes.c_double * len(self.samples))()
+        self._check(self.lib.rlbm_sample_residuals(self.ctx, out))
+        return np.array(out[:])
+
+    def autotune(self):
+        """Times the launch shapes on the current state; returns (bx, grid)."""
+        bx, grid = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.rlbm_autotune(self.ctx, ctypes.byref(bx), ctypes.byref(grid)))
+        return bx.value, grid.value
 
     @property
     def steps_done(self) -> int:
