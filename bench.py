@@ -231,6 +231,9 @@ def gpu_arm(args, rank, world, cpu_line):
     stream = torch.cuda.Stream()
     sv = rlbm.Solver(s, prec=args.prec, stream=stream)
     flush = torch.empty(max(2 * L2_BYTES, 256 << 20), dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        sv.init(0)
+    shape = sv.autotune()
 
     def sync_all():
         torch.cuda.synchronize()
@@ -303,6 +306,9 @@ def gpu_arm(args, rank, world, cpu_line):
                   "bf16dev": "bf16 storage / f32 compute"}[args.prec],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.prec, "sites": sites,
+                   "launch_shape": {"sites_per_block": shape[0] or 128,
+                                    "blocks": shape[1] or "one per tile",
+                                    "kernel": "single-sample" if shape[0] == 0 else "batched"},
                    "l2": "buffer of 2x L2 written before every timed step; steps timed alone",
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -1,0 +1,289 @@
+"""Learned warm start of the relativistic LBM with the spectral neural operator.
+
+    python -m paper_1804_02418_gb300.warmstart [--samples 2000] [--epochs 40] ...
+
+1. Dataset: ensemble-style samples (walled rectangles, two contacts on the
+   y = 0 edge, uniform force along x, seeded per sample) are run to steady
+   state (per-sample residual <= 1e-6) by the batched FP32 solver and
+   resampled onto an N x N canvas.
+2. Training: the operator (fno.FNO) learns (mask, drive, tau, x, y) ->
+   normalised (n, u_x, u_y, T) with its own forward / backward / Adam kernels.
+3. Evaluation: held-out samples are converged from rest (cold) and from the
+   operator's prediction (warm, f = f^eq of the predicted fields); steps and
+   wall time to residual <= 1e-6 are compared.
+
+Normalisation (from the linear Stokes response to a uniform force): with
+nu = 25 (tau - 1/2) / 4 sites^2 / step and the short side W, velocities are
+scaled by F W^2 / nu and density / temperature deviations by F L / 5 (the
+pressure gradient balancing the force over the long side L).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import fno, rlbm, workloads as W
+
+TOL = 1e-6
+
+
+def nu_lattice(tau):
+    return 25.0 * (tau - 0.5) / 4.0
+
+
+def dataset_samples(count, seed0, w_lo=16, w_hi=48, max_aspect=4.0):
+    """Ensemble-style samples small enough to converge in a few thousand steps."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        Wd = int(rng.integers(w_lo, w_hi + 1))
+        a = float(rng.uniform(1.0, max_aspect))
+        L = max(Wd, int(round(a * Wd)))
+        tau = float(rng.uniform(0.6, 2.0))
+        cw = int(rng.integers(4, max(5, Wd // 3) + 1))
+        F = float(10.0 ** rng.uniform(-7.0, -5.0))
+        spacing = max(cw + 2 * W.HOP_RADIUS, L // 4)
+        spacing = min(spacing, L - cw - 2)
+        out.append(W.graphene_sample(nx=L, ny=Wd, contact_width=cw, contact_spacing=spacing,
+                                     force=F, tau=tau))
+    return out
+
+
+def scales(s):
+    u = s.Fx * s.ny ** 2 / nu_lattice(s.tau)
+    d = s.Fx * s.nx / 5.0
+    return d, u
+
+
+def canvas_inputs(s, N):
+    """Input channels on the canvas [N, N, 5] and the mask [N, N].  The
+    sample (nx x ny) is scaled by N / max(nx, ny) and placed at the origin;
+    rows are y, columns x."""
+    M = max(s.nx, s.ny)
+    wc, hc = max(1, round(N * s.nx / M)), max(1, round(N * s.ny / M))
+    x = np.zeros((N, N, 5), dtype=np.float32)
+    mask = np.zeros((N, N), dtype=np.float32)
+    mask[:hc, :wc] = 1.0
+    geo = mask.copy()
+    rows = max(1, round(N / M))                      # canvas rows of the contact edge
+    for c in s.contacts:
+        lo, hi = round(N * c.x0 / M), round(N * (c.x0 + c.length) / M)
+        geo[:rows, lo:hi] = 2.0
+    x[..., 0] = geo
+    x[..., 1] = mask * (math.log10(abs(s.Fx)) + 6.0)
+    x[..., 2] = mask * (s.tau - 1.3) / 0.7
+    jj, ii = np.meshgrid(np.arange(N), np.arange(N))
+    x[..., 3] = jj / N
+    x[..., 4] = ii / N
+    return x, mask, (hc, wc)
+
+
+class Resampler:
+    """Bilinear resampling between sample grids and the canvas (library kernel)."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.lib = fno._lib()
+
+    def __call__(self, planes, dh, dw):
+        t = self.torch
+        src = planes.contiguous().float()
+        nch, sh, sw = src.shape
+        dst = t.empty((nch, dh, dw), dtype=t.float32, device=src.device)
+        fno._ok(self.lib.rlbm_resample_bilinear(fno._p(src), nch, sh, sw, fno._p(dst), dh, dw,
+                                                ctypes_stream(t)), "resample")
+        return dst
+
+
+def ctypes_stream(torch):
+    import ctypes
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=20):
+    """Runs every sample to residual <= TOL; returns (steps per sample, wall seconds,
+    final fields per sample).  init: optional list of (n, ux, uy, T) host arrays."""
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sv = rlbm.Solver(samples, prec=prec, stream=stream, graph_steps=graph_steps)
+        for i in range(len(samples)):
+            if init is None:
+                sv.init(i)
+            else:
+                sv.init(i, *[np.ascontiguousarray(a, dtype=np.float64) for a in init[i]])
+        sv.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = np.full(len(samples), -1, dtype=np.int64)
+        steps = 0
+        while steps < max_steps and (done < 0).any():
+            sv.step(check, residual=True)
+            steps += check
+            r = sv.sample_residuals()
+            newly = (done < 0) & (r <= TOL)
+            done[newly] = steps
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        fields = [sv.moments(i) for i in range(len(samples))]
+        sv.close()
+    done[done < 0] = max_steps
+    return done, wall, fields
+
+
+@dataclass
+class Data:
+    x: np.ndarray        # [S, N, N, 5]
+    y: np.ndarray        # [S, N, N, 4] normalised targets
+    m: np.ndarray        # [S, N, N]
+
+
+def build_dataset(samples, fields, N):
+    import torch
+    rs = Resampler()
+    S = len(samples)
+    X = np.zeros((S, N, N, 5), np.float32)
+    Y = np.zeros((S, N, N, 4), np.float32)
+    Mk = np.zeros((S, N, N), np.float32)
+    for k, (s, f) in enumerate(zip(samples, fields)):
+        x, mask, (hc, wc) = canvas_inputs(s, N)
+        d, u = scales(s)
+        n, ux, uy, T = f
+        planes = torch.tensor(np.stack([(n - 1) / d, ux / u, uy / u, (T - 1) / d]),
+                              dtype=torch.float32, device="cuda")
+        r = rs(planes, hc, wc).cpu().numpy()
+        X[k] = x
+        Mk[k] = mask
+        Y[k, :hc, :wc] = np.moveaxis(r, 0, -1)
+    return Data(X, Y, Mk)
+
+
+def predict_fields(net, samples, N):
+    """Operator prediction -> (n, u_x, u_y, T) on every sample's own grid."""
+    import torch
+    rs = Resampler()
+    out = []
+    B = net.B
+    for k0 in range(0, len(samples), B):
+        chunk = samples[k0:k0 + B]
+        X = np.zeros((B, N, N, 5), np.float32)
+        geo = []
+        for j, s in enumerate(chunk):
+            x, _, hw = canvas_inputs(s, N)
+            X[j] = x
+            geo.append(hw)
+        y = net.forward(torch.tensor(X.reshape(-1, 5), dtype=torch.bfloat16, device="cuda"))
+        y = y.view(B, N, N, 4)
+        for j, s in enumerate(chunk):
+            hc, wc = geo[j]
+            planes = y[j, :hc, :wc].permute(2, 0, 1).contiguous()
+            r = rs(planes, s.ny, s.nx).double().cpu().numpy()
+            d, u = scales(s)
+            n = 1.0 + d * r[0]
+            T = 1.0 + d * r[3]
+            ux, uy = u * r[1], u * r[2]
+            sp = np.sqrt(ux * ux + uy * uy)
+            lim = 0.3
+            fac = np.where(sp > lim, lim / np.maximum(sp, 1e-300), 1.0)
+            out.append((np.clip(n, 0.5, 1.5), ux * fac, uy * fac, np.clip(T, 0.5, 1.5)))
+    return out
+
+
+def train(data, cfg, epochs, batch, lr=2e-3, seed=0, log=None):
+    import torch
+    net = fno.FNO(cfg, batch=batch, seed=seed)
+    S = data.x.shape[0]
+    rng = np.random.default_rng(seed)
+    N = cfg.N
+    X = torch.tensor(data.x.reshape(S, N * N, 5), dtype=torch.bfloat16, device="cuda")
+    Y = torch.tensor(data.y.reshape(S, N * N, 4), dtype=torch.float32, device="cuda")
+    Mk = torch.tensor(data.m.reshape(S, N * N), dtype=torch.float32, device="cuda")
+    steps_per_epoch = max(1, S // batch)
+    total = epochs * steps_per_epoch
+    it = 0
+    history = []
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        perm = rng.permutation(S)
+        acc = 0.0
+        for k in range(steps_per_epoch):
+            idx = torch.tensor(perm[k * batch:(k + 1) * batch], device="cuda")
+            net.forward(X[idx].reshape(-1, 5))
+            loss = net.loss(Y[idx].reshape(-1, 4).contiguous(), Mk[idx].reshape(-1).contiguous())
+            net.backward()
+            it += 1
+            cur = lr * 0.5 * (1.0 + math.cos(math.pi * it / total))     # cosine decay
+            net.adam(lr=cur)
+            acc += float(loss)
+        history.append(acc / steps_per_epoch)
+        if log:
+            log(f"epoch {ep + 1}/{epochs} loss {history[-1]:.4e} ({time.perf_counter() - t0:.1f} s)")
+    torch.cuda.synchronize()
+    return net, history, time.perf_counter() - t0
+
+
+def evaluate(net, data, batch):
+    """Masked MSE of the operator on a dataset (normalised units)."""
+    import torch
+    S = data.x.shape[0]
+    N = net.cfg.N
+    tot, cnt = 0.0, 0
+    for k0 in range(0, S - batch + 1, batch):
+        X = torch.tensor(data.x[k0:k0 + batch].reshape(-1, 5), dtype=torch.bfloat16, device="cuda")
+        Y = torch.tensor(data.y[k0:k0 + batch].reshape(-1, 4), dtype=torch.float32, device="cuda")
+        Mk = torch.tensor(data.m[k0:k0 + batch].reshape(-1), dtype=torch.float32, device="cuda")
+        net.forward(X)
+        tot += float(net.loss(Y, Mk))
+        cnt += 1
+    return tot / max(cnt, 1)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--samples", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--canvas", type=int, default=256)
+    ap.add_argument("--width", type=int, default=32)
+    ap.add_argument("--modes", type=int, default=16)
+    ap.add_argument("--layers", type=int, default=4)
+    ap.add_argument("--seed", type=int, default=20180406)
+    ap.add_argument("--eval-samples", type=int, default=64)
+    args = ap.parse_args()
+    log = lambda m: print(m, flush=True)
+    cfg = fno.FNOConfig(N=args.canvas, C=args.width, Cq=4 * args.width, L=args.layers,
+                        m1=args.modes, m2=args.modes)
+    samples = dataset_samples(args.samples + args.test, args.seed)
+    t0 = time.perf_counter()
+    steps, wall, fields = converge(samples, "f32")
+    log(json.dumps({"phase": "dataset", "samples": len(samples), "sites": int(sum(s.sites for s in samples)),
+                    "steps_max": int(steps.max()), "steps_mean": float(steps.mean()),
+                    "seconds": time.perf_counter() - t0}))
+    data = build_dataset(samples, fields, cfg.N)
+    tr = Data(data.x[:args.samples], data.y[:args.samples], data.m[:args.samples])
+    te = Data(data.x[args.samples:], data.y[args.samples:], data.m[args.samples:])
+    net, hist, secs = train(tr, cfg, args.epochs, args.batch, log=log)
+    log(json.dumps({"phase": "train", "epochs": args.epochs, "seconds": secs,
+                    "train_mse": hist[-1], "test_mse": evaluate(net, te, args.batch),
+                    "target_var": float((te.y ** 2 * te.m[..., None]).sum() / (4 * te.m.sum()))}))
+    held = samples[args.samples:args.samples + args.eval_samples]
+    pred = predict_fields(net, held, cfg.N)
+    for prec in ("f64", "f32"):
+        cold, wc, _ = converge(held, prec)
+        warm, ww, _ = converge(held, prec, init=pred)
+        log(json.dumps({"phase": "warm_start", "precision": prec, "samples": len(held),
+                        "cold_steps_mean": float(cold.mean()), "warm_steps_mean": float(warm.mean()),
+                        "step_ratio": float(warm.mean() / cold.mean()),
+                        "cold_seconds": wc, "warm_seconds": ww,
+                        "warm_fewer_steps_fraction": float((warm < cold).mean())}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,122 @@
+"""Spectral neural operator kernels vs the FP64 oracle (GPU).
+
+* the tensor-core GEMM (every transpose / epilogue / batch-stride mode) on
+  bf16-representable inputs equals the FP64 product to FP32 accumulation
+  accuracy;
+* forward output and all parameter gradients of the GPU network equal the
+  oracle's within BF16 tolerances (weights, activations and DFT matrices are
+  BF16 on the GPU, FP32 accumulation):
+  forward relative L2 <= 3e-2, gradients relative L2 <= 6e-2 per tensor.
+"""
+import numpy as np
+import pytest
+
+from oracle import fno as ofno
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_02418_gb300 import build, fno
+    build.build()
+    return torch, fno
+
+
+def bf16_round(a):
+    import torch
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("M,N,K,batch", [(70, 45, 37, 3), (128, 64, 96, 1), (5, 300, 64, 2)])
+def test_gemm_bf16_matches_fp64(env, tA, tB, M, N, K, batch):
+    torch, fno = env
+    net = fno.FNO(fno.FNOConfig(N=8, C=8, Cq=8, L=1, m1=2, m2=2), batch=1)
+    rng = np.random.default_rng(M + N + K + 7 * tA + 3 * tB)
+    A = bf16_round(rng.standard_normal((batch, K, M) if tA else (batch, M, K)))
+    B = bf16_round(rng.standard_normal((batch, N, K) if tB else (batch, K, N)))
+    bias = rng.standard_normal(N)
+    C0 = rng.standard_normal((batch, M, N))
+    At = torch.tensor(A, dtype=torch.bfloat16, device="cuda")
+    Bt = torch.tensor(B, dtype=torch.bfloat16, device="cuda")
+    Ct = torch.tensor(C0, dtype=torch.float32, device="cuda")
+    bt = torch.tensor(bias, dtype=torch.float32, device="cuda")
+    Dt = torch.empty((batch, M, N), dtype=torch.bfloat16, device="cuda")
+    net.gemm(At, Bt, M, N, K, lda=M if tA else K, ldb=K if tB else N, transA=tA, transB=tB,
+             C=Ct, ldc=N, D=Dt, bias=bt, beta=0.5, epi=fno.EPI_GELU, batch=batch,
+             sA=M * K, sB=K * N, sC=M * N, alpha=2.0)
+    torch.cuda.synchronize()
+    opA = np.transpose(A, (0, 2, 1)) if tA else A
+    opB = np.transpose(B, (0, 2, 1)) if tB else B
+    ref = 2.0 * opA @ opB + 0.5 * C0 + bias
+    got = Ct.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * (np.abs(opA) @ np.abs(opB)).max() * 2 + 1e-5
+    g = ofno.gelu(ref)
+    assert np.abs(Dt.float().cpu().numpy() - g).max() <= 1e-2 * max(1.0, np.abs(g).max())
+    # split-K atomic accumulation over the batch into one output
+    Ca = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    net.gemm(At, Bt, M, N, K, lda=M if tA else K, ldb=K if tB else N, transA=tA, transB=tB,
+             C=Ca, ldc=N, epi=fno.EPI_ATOMIC, batch=batch, sA=M * K, sB=K * N, sC=0)
+    torch.cuda.synchronize()
+    assert np.abs(Ca.cpu().numpy() - (opA @ opB).sum(0)).max() <= 1e-4 * batch * (np.abs(opA) @ np.abs(opB)).max()
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-30)
+
+
+def test_forward_and_gradients_match_oracle(env):
+    torch, fno = env
+    cfg = fno.FNOConfig(N=32, C=8, Cq=16, L=2, m1=4, m2=5)
+    B = 2
+    net = fno.FNO(cfg, batch=B, seed=3)
+    rng = np.random.default_rng(4)
+    x = bf16_round(rng.standard_normal((B, cfg.N, cfg.N, cfg.cin)))
+    t = rng.standard_normal((B, cfg.N, cfg.N, cfg.cout))
+    m = (rng.uniform(size=(B, cfg.N, cfg.N)) < 0.8).astype(float)
+    rows = B * cfg.N * cfg.N
+    x16 = torch.tensor(x.reshape(rows, cfg.cin), dtype=torch.bfloat16, device="cuda")
+    tt = torch.tensor(t.reshape(rows, cfg.cout), dtype=torch.float32, device="cuda")
+    mt = torch.tensor(m.reshape(rows), dtype=torch.float32, device="cuda")
+    y = net.forward(x16)
+    loss = net.loss(tt, mt)
+    net.backward()
+    torch.cuda.synchronize()
+    # oracle with the same (bf16-rounded) weights the GPU GEMMs use
+    pg = net.params_numpy()
+    p = {k: (bf16_round(v) if k in ("P", "W", "Q1", "Q2") else v) for k, v in pg.items()}
+    p["R"] = pg["R"][..., 0] + 1j * pg["R"][..., 1]
+    o = ofno.Oracle(cfg.N, cfg.m1, cfg.m2)
+    yo, cache = o.forward(p, x)
+    lo, dyo = o.loss(yo, t, m)
+    go = o.backward(p, cache, dyo)
+    assert rel_l2(y.cpu().numpy().reshape(yo.shape), yo) < 3e-2
+    assert abs(float(loss) - lo) < 3e-2 * lo
+    for name in ("P", "bp", "W", "b", "Q1", "bq1", "Q2", "bq2"):
+        g = net.get(name, "grad").cpu().numpy()
+        assert rel_l2(g, go[name]) < 6e-2, name
+    gR = net.get("R", "grad").cpu().numpy()
+    assert rel_l2(gR[..., 0] + 1j * gR[..., 1], go["R"]) < 6e-2
+
+
+def test_adam_step_reduces_loss(env):
+    torch, fno = env
+    cfg = fno.FNOConfig(N=32, C=8, Cq=16, L=2, m1=4, m2=5)
+    B = 2
+    net = fno.FNO(cfg, batch=B, seed=5)
+    rng = np.random.default_rng(6)
+    rows = B * cfg.N * cfg.N
+    x16 = torch.tensor(rng.standard_normal((rows, cfg.cin)), dtype=torch.bfloat16, device="cuda")
+    tt = torch.tensor(0.1 * rng.standard_normal((rows, cfg.cout)), dtype=torch.float32, device="cuda")
+    mt = torch.ones(rows, dtype=torch.float32, device="cuda")
+    losses = []
+    for _ in range(30):
+        net.forward(x16)
+        losses.append(float(net.loss(tt, mt)))
+        net.backward()
+        net.adam(lr=3e-3)
+    assert losses[-1] < 0.7 * losses[0]

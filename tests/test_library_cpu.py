@@ -13,7 +13,7 @@ import re
 import numpy as np
 import pytest
 
-from paper_1804_02418_gb300 import rlbm, workloads
+from paper_1804_02418_gb300 import fno, rlbm, workloads  # fno registers its exports
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
