@@ -106,11 +106,14 @@ def ctypes_stream(torch):
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=20):
+def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=20, ref=None):
     """Runs every sample to residual <= TOL; returns (steps per sample, wall seconds,
-    final fields per sample).  init: optional list of (n, ux, uy, T) host arrays."""
+    final fields per sample, distances).  init: optional list of (n, ux, uy, T)
+    host arrays.  ref: optional reference steady fields; then `distances` holds,
+    per check and sample, ||u(t) - u_ref|| / ||u_ref|| (else None)."""
     import torch
     stream = torch.cuda.Stream()
+    dist = [] if ref is not None else None
     with torch.cuda.stream(stream):
         sv = rlbm.Solver(samples, prec=prec, stream=stream, graph_steps=graph_steps)
         for i in range(len(samples)):
@@ -129,12 +132,30 @@ def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=2
             r = sv.sample_residuals()
             newly = (done < 0) & (r <= TOL)
             done[newly] = steps
+            if ref is not None:
+                row = []
+                for i in range(len(samples)):
+                    _, ux, uy, _ = sv.moments(i)
+                    rx, ry = ref[i][1], ref[i][2]
+                    row.append(float(np.sqrt(((ux - rx) ** 2 + (uy - ry) ** 2).sum()
+                                             / max((rx ** 2 + ry ** 2).sum(), 1e-300))))
+                dist.append(row)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         fields = [sv.moments(i) for i in range(len(samples))]
         sv.close()
     done[done < 0] = max_steps
-    return done, wall, fields
+    return done, wall, fields, (np.array(dist) if dist is not None else None)
+
+
+def steps_to(dist, level, check=100):
+    """First check (in steps) at which each sample's distance is <= level."""
+    out = np.full(dist.shape[1], dist.shape[0] * check)
+    for i in range(dist.shape[1]):
+        hit = np.nonzero(dist[:, i] <= level)[0]
+        if hit.size:
+            out[i] = (hit[0] + 1) * check
+    return out
 
 
 @dataclass
@@ -164,7 +185,40 @@ def build_dataset(samples, fields, N):
     return Data(X, Y, Mk)
 
 
-def predict_fields(net, samples, N):
+def canvas_to_fields(rs, y, s, N, use=("n", "u", "T"), chan=None):
+    """Normalised canvas fields y (tensor [N, N, 4]) -> (n, u_x, u_y, T) host
+    arrays on the sample grid [ny][nx].  chan: per-channel standard scales the
+    targets were divided by (None: 1).  Fields not in `use` are set to their
+    rest values (n = T = 1, u = 0)."""
+    M = max(s.nx, s.ny)
+    wc, hc = max(1, round(N * s.nx / M)), max(1, round(N * s.ny / M))
+    planes = y[:hc, :wc].permute(2, 0, 1).contiguous()
+    r = rs(planes, s.ny, s.nx).double().cpu().numpy()
+    if chan is not None:
+        r = r * np.asarray(chan, dtype=np.float64)[:, None, None]
+    d, u = scales(s)
+    n = 1.0 + d * r[0]
+    T = 1.0 + d * r[3]
+    ux, uy = u * r[1], u * r[2]
+    sp = np.sqrt(ux * ux + uy * uy)
+    lim = 0.3
+    fac = np.where(sp > lim, lim / np.maximum(sp, 1e-300), 1.0)
+    if "n_anchor" in use:
+        # the contacts hold n = 1: shift the predicted density so that the
+        # sites beside the contacts sit at the contact value
+        vals = [n[0, c.x0:c.x0 + c.length] for c in s.contacts if c.edge == 0]
+        if vals:
+            n = n - np.concatenate(vals).mean() + 1.0
+    elif "n" not in use:
+        n = np.ones_like(n)
+    if "T" not in use:
+        T = np.ones_like(T)
+    if "u" not in use:
+        ux, uy, fac = np.zeros_like(ux), np.zeros_like(uy), 1.0
+    return (np.clip(n, 0.5, 1.5), ux * fac, uy * fac, np.clip(T, 0.5, 1.5))
+
+
+def predict_fields(net, samples, N, use=("n", "u", "T"), chan=None):
     """Operator prediction -> (n, u_x, u_y, T) on every sample's own grid."""
     import torch
     rs = Resampler()
@@ -173,25 +227,12 @@ def predict_fields(net, samples, N):
     for k0 in range(0, len(samples), B):
         chunk = samples[k0:k0 + B]
         X = np.zeros((B, N, N, 5), np.float32)
-        geo = []
         for j, s in enumerate(chunk):
-            x, _, hw = canvas_inputs(s, N)
-            X[j] = x
-            geo.append(hw)
+            X[j] = canvas_inputs(s, N)[0]
         y = net.forward(torch.tensor(X.reshape(-1, 5), dtype=torch.bfloat16, device="cuda"))
         y = y.view(B, N, N, 4)
         for j, s in enumerate(chunk):
-            hc, wc = geo[j]
-            planes = y[j, :hc, :wc].permute(2, 0, 1).contiguous()
-            r = rs(planes, s.ny, s.nx).double().cpu().numpy()
-            d, u = scales(s)
-            n = 1.0 + d * r[0]
-            T = 1.0 + d * r[3]
-            ux, uy = u * r[1], u * r[2]
-            sp = np.sqrt(ux * ux + uy * uy)
-            lim = 0.3
-            fac = np.where(sp > lim, lim / np.maximum(sp, 1e-300), 1.0)
-            out.append((np.clip(n, 0.5, 1.5), ux * fac, uy * fac, np.clip(T, 0.5, 1.5)))
+            out.append(canvas_to_fields(rs, y[j], s, N, use, chan))
     return out
 
 
@@ -262,11 +303,19 @@ def main():
                         m1=args.modes, m2=args.modes)
     samples = dataset_samples(args.samples + args.test, args.seed)
     t0 = time.perf_counter()
-    steps, wall, fields = converge(samples, "f32")
+    steps, wall, fields, _ = converge(samples, "f32")
     log(json.dumps({"phase": "dataset", "samples": len(samples), "sites": int(sum(s.sites for s in samples)),
                     "steps_max": int(steps.max()), "steps_mean": float(steps.mean()),
                     "seconds": time.perf_counter() - t0}))
     data = build_dataset(samples, fields, cfg.N)
+    # standardise every target channel over the training set (the physical
+    # scales above fix the per-sample dependence on F, tau and size; the
+    # channels still differ by orders of magnitude)
+    m_tr = data.m[:args.samples, ..., None]
+    chan = np.sqrt((data.y[:args.samples] ** 2 * m_tr).sum((0, 1, 2)) / max(m_tr.sum(), 1.0))
+    chan = np.where(chan > 0, chan, 1.0).astype(np.float32)
+    data.y /= chan
+    log(json.dumps({"phase": "normalisation", "channel_scales": chan.tolist()}))
     tr = Data(data.x[:args.samples], data.y[:args.samples], data.m[:args.samples])
     te = Data(data.x[args.samples:], data.y[args.samples:], data.m[args.samples:])
     net, hist, secs = train(tr, cfg, args.epochs, args.batch, log=log)
@@ -274,15 +323,30 @@ def main():
                     "train_mse": hist[-1], "test_mse": evaluate(net, te, args.batch),
                     "target_var": float((te.y ** 2 * te.m[..., None]).sum() / (4 * te.m.sum()))}))
     held = samples[args.samples:args.samples + args.eval_samples]
-    pred = predict_fields(net, held, cfg.N)
+    ref = fields[args.samples:args.samples + args.eval_samples]
+    cold = {}
     for prec in ("f64", "f32"):
-        cold, wc, _ = converge(held, prec)
-        warm, ww, _ = converge(held, prec, init=pred)
-        log(json.dumps({"phase": "warm_start", "precision": prec, "samples": len(held),
-                        "cold_steps_mean": float(cold.mean()), "warm_steps_mean": float(warm.mean()),
-                        "step_ratio": float(warm.mean() / cold.mean()),
-                        "cold_seconds": wc, "warm_seconds": ww,
-                        "warm_fewer_steps_fraction": float((warm < cold).mean())}))
+        c_steps, c_wall, _, c_dist = converge(held, prec, ref=ref, max_steps=20000)
+        cold[prec] = (c_steps, c_wall, c_dist)
+        log(json.dumps({"phase": "cold", "precision": prec, "samples": len(held),
+                        "steps_mean": float(c_steps.mean()), "seconds": c_wall}))
+    for use in (("u",), ("n", "u"), ("n_anchor", "u")):
+        pred = predict_fields(net, held, cfg.N, use=use, chan=chan)
+        err = [float(np.sqrt(((p[1] - r[1]) ** 2 + (p[2] - r[2]) ** 2).sum() / max((r[1] ** 2 + r[2] ** 2).sum(), 1e-300)))
+               for p, r in zip(pred, ref)]
+        for prec in ("f64", "f32"):
+            w_steps, w_wall, _, w_dist = converge(held, prec, init=pred, ref=ref, max_steps=20000)
+            c_steps, c_wall, c_dist = cold[prec]
+            line = {"phase": "warm_start", "fields": "+".join(use), "precision": prec,
+                    "samples": len(held), "u_rel_error_initial_median": float(np.median(err)),
+                    "cold_steps_mean": float(c_steps.mean()), "warm_steps_mean": float(w_steps.mean()),
+                    "step_ratio": float(w_steps.mean() / c_steps.mean()),
+                    "cold_seconds": c_wall, "warm_seconds": w_wall,
+                    "warm_fewer_steps_fraction": float((w_steps < c_steps).mean())}
+            for lvl in (0.3, 0.1, 0.03, 0.01):
+                cs, ws_ = steps_to(c_dist, lvl), steps_to(w_dist, lvl)
+                line[f"steps_to_u_within_{lvl}"] = {"cold": float(np.median(cs)), "warm": float(np.median(ws_))}
+            log(json.dumps(line))
 
 
 if __name__ == "__main__":
