@@ -1,0 +1,88 @@
+"""Physics checks of the GPU path on the paper's geometry (GPU).
+
+* Whirlpools: with current injected at one contact and withdrawn at the
+  other (no body force, the vicinity geometry of Sec. 3), the flow along the
+  edge reverses beside both contacts: the edge-parallel velocity changes sign
+  outside the injector and outside the collector (symmetric back-flow).  With
+  the uniform body force of the benchmark sample, the vorticity changes sign
+  beside the injector.
+* Viscosity: the transverse shear wave decays at nu k^2 with
+  nu = (tau - 1/2) c^2 / 4, c = 5 sites per step (within 1 % at 64^2).
+"""
+import numpy as np
+import pytest
+
+from paper_1804_02418_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_02418_gb300 import build, rlbm
+    build.build()
+    return rlbm
+
+
+def steady(rl, s, steps=100000):
+    with rl.Solver(s, prec="f32", graph_steps=20) as sv:
+        sv.init(0)
+        sv.autotune()
+        sv.step(steps)
+        n, ux, uy, T = sv.moments(0)
+        sv.check()
+    return n, ux, uy, T
+
+
+def sign_changes(v):
+    return np.nonzero(np.diff(np.sign(v)) != 0)[0]
+
+
+def test_injected_current_makes_whirlpools_beside_both_contacts(rl):
+    s = W.graphene_sample(force=0.0, u_in=1e-5)
+    n, ux, uy, T = steady(rl, s)
+    inj = s.contacts[0].x0 + s.contacts[0].length // 2            # 384
+    col = s.contacts[1].x0 + s.contacts[1].length // 2            # 640
+    for y in (8, 16, 32):
+        row = ux[y]
+        left = sign_changes(row[100:inj - 40]) + 100
+        right = sign_changes(row[col + 40:s.nx - 100]) + col + 40
+        assert left.size >= 1, (y, "no back-flow beside the injector")
+        assert right.size >= 1, (y, "no back-flow beside the collector")
+        # mirror symmetry about the midpoint between the contacts
+        mid = 0.5 * (inj + col)
+        assert abs((mid - left[-1]) - (right[0] - mid)) < 40, (y, left, right)
+    # inflow at the injector, outflow at the collector
+    assert uy[2, inj] > 0 and uy[2, col] < 0
+
+
+def test_body_force_sample_vorticity_changes_sign_beside_injector(rl):
+    s = W.graphene_sample()
+    n, ux, uy, T = steady(rl, s)
+    w = np.zeros_like(ux)
+    w[1:-1, 1:-1] = 0.5 * (uy[1:-1, 2:] - uy[1:-1, :-2]) - 0.5 * (ux[2:, 1:-1] - ux[:-2, 1:-1])
+    inj = s.contacts[0].x0 + s.contacts[0].length // 2
+    for y in (8, 16):
+        ch = sign_changes(w[y, 100:inj - 20]) + 100
+        assert ch.size >= 1, y
+
+
+def test_shear_wave_viscosity_on_gpu(rl):
+    tau, n = 0.8, 64
+    s = W.shear_wave(n, tau)
+    fields = [np.ascontiguousarray(f) for f in W.shear_wave_fields(s)]
+    basis = np.sin(2 * np.pi * np.arange(n) / n)
+    amps = []
+    with rl.Solver(s, prec="f64") as sv:
+        sv.init(0, *fields)
+        for k in range(10):
+            sv.step(50)
+            ux = sv.moments(0)[1]
+            amps.append(2.0 / (n * n) * np.sum(ux * basis[:, None]))
+    t = 50 * np.arange(1, 11)
+    rate = -np.polyfit(t[1:], np.log(amps[1:]), 1)[0]
+    nu = (tau - 0.5) * 25.0 / 4.0
+    assert abs(rate / (nu * (2 * np.pi / n) ** 2) - 1.0) < 0.01
