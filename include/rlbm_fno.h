@@ -43,6 +43,25 @@ int rlbm_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha,
                    float beta, float* C, long long ldc, long long strideC,
                    const float* bias, void* D, int epilogue, int batch, void* stream);
 
+/* The same operation as rlbm_gemm_bf16 (same arguments, layouts and
+ * epilogues) on the fifth-generation tensor cores: one CTA per 128 x 64
+ * output tile, operands staged in shared memory, tcgen05.mma (M 128, N 64,
+ * K 16, BF16 x BF16 -> FP32) accumulating in tensor memory, read back with
+ * tcgen05.ld for the epilogue.  The summation order over K differs from
+ * rlbm_gemm_bf16, so the two agree to FP32 rounding, not bit for bit.  Every
+ * wait inside the kernel is bounded (about 2 s); a CTA that gives up skips
+ * its tile and sets a device flag that rlbm_gemm_tc_error reports. */
+int rlbm_gemm_bf16_tc(int transA, int transB, int M, int N, int K, float alpha,
+                      const void* A, long long lda, long long strideA,
+                      const void* B, long long ldb, long long strideB,
+                      float beta, float* C, long long ldc, long long strideC,
+                      const float* bias, void* D, int epilogue, int batch, void* stream);
+
+/* Reads (and clears) the timeout flag of rlbm_gemm_bf16_tc on the current
+ * device: *flag = 0 if no CTA gave up since the last call.  Synchronous with
+ * respect to the device (the read waits for prior work). */
+int rlbm_gemm_tc_error(int* flag);
+
 /* Per-mode complex channel mixing of the spectral layer.
  * S, U: f32 [batch][KX][2][KY][C] (re / im planes per kx), R: f32
  * [KX][KY][C][C][2] (re, im), U(b, kx, ky, o) = sum_i S(b, kx, ky, i) R(kx, ky, i, o). */

@@ -144,6 +144,178 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
 }
 
 // ---------------------------------------------------------------------------
+// Fifth-generation tensor-core GEMM (tcgen05 / TMEM), one CTA per 128 x 64
+// output tile.  Four warps stage K slabs of 64 into shared memory in the
+// canonical no-swizzle K-major layout (8 x 16-byte core matrices: the two
+// 8-element halves of a K16 step are LBO = 128 B apart, consecutive 8-row
+// groups SBO = 1024 B apart); one thread issues four tcgen05.mma (M = 128,
+// N = 64, K = 16, BF16 x BF16 -> FP32 in TMEM) per slab and commits them to
+// an mbarrier; the accumulator is read back with tcgen05.ld (warp w owns TMEM
+// lanes 32 w .. 32 w + 31 = output rows).  Every wait is bounded: on timeout
+// the CTA raises the error flag, skips its tile, frees its TMEM and returns.
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_N = 64, TC_K = 64;
+constexpr long long kTcSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ unsigned g_tc_error = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Matrix descriptor: start >> 4 [0,14), LBO >> 4 [16,30), SBO >> 4 [32,46),
+// version 1 [46,48), base offset 0, LBO mode 0, layout 0 (no swizzle) [61,64).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | (1ULL << 46);
+}
+
+// Instruction descriptor, kind::f16: D F32 (bit 4), A BF16 (bit 7), B BF16
+// (bit 10), both K-major, N >> 3 at [17,23), M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+         ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kTcSpinCycles) return false;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
+  __shared__ __align__(1024) uint8_t sA[TC_M * TC_K * 2];
+  __shared__ __align__(1024) uint8_t sB[TC_N * TC_K * 2];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_tile;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+  const long long b = blockIdx.z;
+  const __nv_bfloat16* A = g.A + b * g.strideA;
+  const __nv_bfloat16* B = g.B + b * g.strideB;
+  const uint32_t bar = smem_u32(&mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 :: "r"(smem_u32(&tmem_slot)), "r"(TC_N) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_tile = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(sA);
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(sB);
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  const int nslab = (g.K + TC_K - 1) / TC_K;
+  int issued = 0;   // slabs whose MMAs were committed (same value in every thread)
+  for (int sl = 0; sl < nslab; ++sl) {
+    if (sl > 0) {
+      // the MMAs of the previous slab must have read shared memory
+      if (!mbar_wait(bar, (sl - 1) & 1)) abort_tile = 1;
+      __syncthreads();
+      if (abort_tile) break;
+    }
+    const int k0 = sl * TC_K;
+    // element (row, k) of a slab -> core matrix (row / 8, k / 8), 8 core matrices per row group
+    for (int i = tid; i < TC_M * TC_K; i += 128) {
+      int m, k;
+      if (!g.transA) { m = i / TC_K; k = i % TC_K; } else { k = i / TC_M; m = i % TC_M; }
+      const int gm = m0 + m, gk = k0 + k;
+      __nv_bfloat16 v = zero;
+      if (gm < g.M && gk < g.K) v = g.transA ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
+      As[((m >> 3) * 8 + (k >> 3)) * 64 + (m & 7) * 8 + (k & 7)] = v;
+    }
+    for (int i = tid; i < TC_N * TC_K; i += 128) {
+      int n, k;
+      if (!g.transB) { k = i / TC_N; n = i % TC_N; } else { n = i / TC_K; k = i % TC_K; }
+      const int gn = n0 + n, gk = k0 + k;
+      __nv_bfloat16 v = zero;
+      if (gn < g.N && gk < g.K) v = g.transB ? B[(long long)gn * g.ldb + gk] : B[(long long)gk * g.ldb + gn];
+      Bs[((n >> 3) * 8 + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < TC_K / 16; ++kk) {
+        const uint64_t da = tc_desc(a_base + kk * 256, 128, 1024);
+        const uint64_t db = tc_desc(b_base + kk * 256, 128, 1024);
+        const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            :: "r"(tmem), "l"(da), "l"(db), "r"(tc_idesc()), "r"(acc) : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                   :: "r"(bar) : "memory");
+    }
+    issued = sl + 1;
+  }
+  if (!abort_tile) {
+    if (!mbar_wait(bar, (nslab - 1) & 1)) abort_tile = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (!abort_tile) {
+    float* C = g.C ? g.C + b * g.strideC : nullptr;
+    __nv_bfloat16* D = g.D ? g.D + b * g.strideC : nullptr;
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < TC_N; c0 += 8) {
+      uint32_t r[8];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (row < g.M) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int col = n0 + c0 + e;
+          if (col >= g.N) continue;
+          const long long o = (long long)row * g.ldc + col;
+          float v = g.alpha * __uint_as_float(r[e]);
+          if (g.epilogue == RLBM_EPI_ATOMIC) {
+            atomicAdd(C + o, v);
+            continue;
+          }
+          if (C && g.beta != 0.f) v += g.beta * C[o];
+          if (g.bias) v += g.bias[col];
+          if (C) C[o] = v;
+          if (D) D[o] = __float2bfloat16_rn(g.epilogue == RLBM_EPI_GELU ? gelu(v) : v);
+        }
+      }
+    }
+  } else {
+    if (tid == 0) atomicOr(&g_tc_error, 1u);
+    // let the last committed MMAs finish (bounded) before the TMEM is freed
+    if (issued > 0) mbar_wait(bar, (issued - 1) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(TC_N)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Spectral mixing.  S, U: [batch][KX][2][KY][C]; R: [KX][KY][C][C][2].
 // ---------------------------------------------------------------------------
 __global__ void k_mix_fwd(const float* __restrict__ S, const float* __restrict__ R,
@@ -356,6 +528,38 @@ int rlbm_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, con
   if (grid.y > 65535) return RLBM_EINVAL;
   k_gemm<<<grid, kGemmThreads, 0, static_cast<cudaStream_t>(stream)>>>(g);
   return status();
+}
+
+int rlbm_gemm_bf16_tc(int transA, int transB, int M, int N, int K, float alpha, const void* A,
+                      long long lda, long long strideA, const void* B, long long ldb,
+                      long long strideB, float beta, float* C, long long ldc, long long strideC,
+                      const float* bias, void* D, int epilogue, int batch, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0 || !A || !B) return RLBM_EINVAL;
+  if (!C && !D) return RLBM_EINVAL;
+  if (epilogue == RLBM_EPI_ATOMIC && !C) return RLBM_EINVAL;
+  if (epilogue < 0 || epilogue > 2 || batch > 65535) return RLBM_EINVAL;
+  GemmArgs g;
+  g.transA = transA; g.transB = transB; g.M = M; g.N = N; g.K = K;
+  g.alpha = alpha; g.beta = C ? beta : 0.f;
+  g.A = static_cast<const __nv_bfloat16*>(A); g.lda = lda; g.strideA = strideA;
+  g.B = static_cast<const __nv_bfloat16*>(B); g.ldb = ldb; g.strideB = strideB;
+  g.C = C; g.ldc = ldc; g.strideC = strideC;
+  g.bias = bias; g.D = static_cast<__nv_bfloat16*>(D); g.epilogue = epilogue;
+  dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M, batch);
+  if (grid.y > 65535) return RLBM_EINVAL;
+  k_gemm_tc<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(g);
+  return status();
+}
+
+int rlbm_gemm_tc_error(int* flag) {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof v) != cudaSuccess) return RLBM_ECUDA;
+  if (flag) *flag = (int)v;
+  if (v) {
+    const unsigned z = 0;
+    cudaMemcpyToSymbol(g_tc_error, &z, sizeof z);
+  }
+  return RLBM_OK;
 }
 
 int rlbm_fno_mix_forward(const float* S, const float* R, float* U, int batch, int KX, int KY,

@@ -30,6 +30,9 @@ import numpy as np
 from . import rlbm
 
 EPI_NONE, EPI_GELU, EPI_ATOMIC = 0, 1, 2
+# GEMM back ends: "mma" = warp-level mma.sync m16n8k16, "tc" = tcgen05 with
+# the accumulator in tensor memory
+GEMM_IMPLS = {"mma": "rlbm_gemm_bf16", "tc": "rlbm_gemm_bf16_tc"}
 
 _FNO_EXPORTS = {
     "rlbm_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -39,6 +42,7 @@ _FNO_EXPORTS = {
                                       ctypes.c_float, ctypes.c_void_p, ctypes.c_longlong,
                                       ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "rlbm_gemm_tc_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "rlbm_fno_mix_forward": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
     "rlbm_fno_mix_backward": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_int] * 4 + [ctypes.c_void_p]),
     "rlbm_fno_gelu_backward": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p]),
@@ -49,6 +53,7 @@ _FNO_EXPORTS = {
     "rlbm_resample_bilinear": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
 }
+_FNO_EXPORTS["rlbm_gemm_bf16_tc"] = _FNO_EXPORTS["rlbm_gemm_bf16"]
 rlbm.EXPORTS.update(_FNO_EXPORTS)
 
 
@@ -110,11 +115,15 @@ class FNO:
     """Parameters live in one flat FP32 vector (Adam state alongside) with a
     BF16 shadow used by the GEMMs."""
 
-    def __init__(self, cfg: FNOConfig, batch: int, seed: int = 0, device="cuda"):
+    def __init__(self, cfg: FNOConfig, batch: int, seed: int = 0, device="cuda",
+                 gemm_impl: str = "mma"):
         import torch
         self.torch = torch
         self.cfg, self.B = cfg, batch
         self.lib = _lib()
+        if gemm_impl not in GEMM_IMPLS:
+            raise ValueError(f"gemm_impl must be one of {sorted(GEMM_IMPLS)}")
+        self._gemm_fn = getattr(self.lib, GEMM_IMPLS[gemm_impl])
         N, C, Cq, L, m1, m2, cin = cfg.N, cfg.C, cfg.Cq, cfg.L, cfg.m1, cfg.m2, cfg.cin
         KX = 2 * m1
         self.KX = KX
@@ -208,7 +217,7 @@ class FNO:
 
     def gemm(self, A, B, M, N, K, *, lda, ldb, transA=0, transB=0, C=None, ldc=None, D=None,
              bias=None, beta=0.0, epi=EPI_NONE, batch=1, sA=0, sB=0, sC=0, alpha=1.0):
-        rc = self.lib.rlbm_gemm_bf16(transA, transB, M, N, K, alpha, _p(A), lda, sA, _p(B), ldb, sB,
+        rc = self._gemm_fn(transA, transB, M, N, K, alpha, _p(A), lda, sA, _p(B), ldb, sB,
                                      beta, _p(C), ldc if ldc is not None else N, sC, _p(bias),
                                      _p(D), epi, batch, self._stream())
         _ok(rc, "gemm")

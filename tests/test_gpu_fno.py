@@ -1,8 +1,9 @@
 """Spectral neural operator kernels vs the FP64 oracle (GPU).
 
-* the tensor-core GEMM (every transpose / epilogue / batch-stride mode) on
-  bf16-representable inputs equals the FP64 product to FP32 accumulation
-  accuracy;
+* both tensor-core GEMMs (warp-level mma.sync and tcgen05 with a tensor-memory
+  accumulator; every transpose / epilogue / batch-stride mode, ragged tiles)
+  on bf16-representable inputs equal the FP64 product to FP32 accumulation
+  accuracy, and agree with each other on the full-size operator's shapes;
 * forward output and all parameter gradients of the GPU network equal the
   oracle's within BF16 tolerances (weights, activations and DFT matrices are
   BF16 on the GPU, FP32 accumulation):
@@ -31,11 +32,13 @@ def bf16_round(a):
     return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
 
 
+@pytest.mark.parametrize("impl", ["mma", "tc"])
 @pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1), (1, 1)])
-@pytest.mark.parametrize("M,N,K,batch", [(70, 45, 37, 3), (128, 64, 96, 1), (5, 300, 64, 2)])
-def test_gemm_bf16_matches_fp64(env, tA, tB, M, N, K, batch):
+@pytest.mark.parametrize("M,N,K,batch", [(70, 45, 37, 3), (128, 64, 96, 1), (5, 300, 64, 2),
+                                         (257, 129, 333, 2), (1, 1, 1, 1)])
+def test_gemm_bf16_matches_fp64(env, impl, tA, tB, M, N, K, batch):
     torch, fno = env
-    net = fno.FNO(fno.FNOConfig(N=8, C=8, Cq=8, L=1, m1=2, m2=2), batch=1)
+    net = fno.FNO(fno.FNOConfig(N=8, C=8, Cq=8, L=1, m1=2, m2=2), batch=1, gemm_impl=impl)
     rng = np.random.default_rng(M + N + K + 7 * tA + 3 * tB)
     A = bf16_round(rng.standard_normal((batch, K, M) if tA else (batch, M, K)))
     B = bf16_round(rng.standard_normal((batch, N, K) if tB else (batch, K, N)))
@@ -63,17 +66,53 @@ def test_gemm_bf16_matches_fp64(env, tA, tB, M, N, K, batch):
              C=Ca, ldc=N, epi=fno.EPI_ATOMIC, batch=batch, sA=M * K, sB=K * N, sC=0)
     torch.cuda.synchronize()
     assert np.abs(Ca.cpu().numpy() - (opA @ opB).sum(0)).max() <= 1e-4 * batch * (np.abs(opA) @ np.abs(opB)).max()
+    assert tc_flag(fno) == 0
+
+
+def tc_flag(fno):
+    import ctypes
+    f = ctypes.c_int(-1)
+    assert fno._lib().rlbm_gemm_tc_error(ctypes.byref(f)) == 0
+    return f.value
+
+
+def test_tcgen05_and_mma_agree_on_the_operator_shapes(env):
+    """The spectral-layer shapes of the full-size operator (N 256, C 32,
+    m1 = m2 = 16, batch 8): the two back ends agree to FP32 accumulation."""
+    torch, fno = env
+    rng = np.random.default_rng(11)
+    N, C, m2, B = 256, 32, 16, 8
+    cases = [  # (M, N, K, batch, lda, ldb): y-DFT, x-DFT, pointwise W
+        (2 * m2, C, N, B * N, N, C),
+        (64, m2 * C, 2 * N, B, 2 * N, m2 * C),
+        (B * N * N, C, C, 1, C, C),
+    ]
+    for M, Nn, K, batch, lda, ldb in cases:
+        A = torch.tensor(rng.standard_normal((M, K)), dtype=torch.bfloat16, device="cuda")
+        Bm = torch.tensor(rng.standard_normal((batch, K, Nn)), dtype=torch.bfloat16, device="cuda")
+        outs = []
+        for impl in ("mma", "tc"):
+            net = fno.FNO(fno.FNOConfig(N=8, C=8, Cq=8, L=1, m1=2, m2=2), batch=1, gemm_impl=impl)
+            Cm = torch.empty((batch, M, Nn), dtype=torch.float32, device="cuda")
+            net.gemm(A, Bm, M, Nn, K, lda=lda, ldb=ldb, C=Cm, ldc=Nn, batch=batch, sA=0,
+                     sB=K * Nn, sC=M * Nn)
+            outs.append(Cm)
+        torch.cuda.synchronize()
+        scale = float((A.float().abs() @ Bm[0].float().abs()).max())
+        assert float((outs[0] - outs[1]).abs().max()) <= 2e-6 * scale * max(1.0, K / 64)
+    assert tc_flag(fno) == 0
 
 
 def rel_l2(a, b):
     return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-30)
 
 
-def test_forward_and_gradients_match_oracle(env):
+@pytest.mark.parametrize("impl", ["mma", "tc"])
+def test_forward_and_gradients_match_oracle(env, impl):
     torch, fno = env
     cfg = fno.FNOConfig(N=32, C=8, Cq=16, L=2, m1=4, m2=5)
     B = 2
-    net = fno.FNO(cfg, batch=B, seed=3)
+    net = fno.FNO(cfg, batch=B, seed=3, gemm_impl=impl)
     rng = np.random.default_rng(4)
     x = bf16_round(rng.standard_normal((B, cfg.N, cfg.N, cfg.cin)))
     t = rng.standard_normal((B, cfg.N, cfg.N, cfg.cout))
