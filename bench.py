@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--prec", default="f32", choices=sorted(BYTES))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-steps", type=int, default=12)
+    ap.add_argument("--tune-cache", default=None,
+                    help="file where the launch-shape autotuner keeps its choice (a later run "
+                         "with the same file reuses it instead of timing the candidates)")
     ap.add_argument("--workload", default="graphene", choices=["graphene", "ensemble"],
                     help="graphene: the 1024x512 sample (default line); ensemble: the "
                          "256-sample uneven ensemble, sharded by sample over the ranks")
@@ -233,8 +236,18 @@ def gpu_arm(args, rank, world, cpu_line):
     s = W.graphene_sample()
     sites = s.sites
     stream = torch.cuda.Stream()
-    sv = rlbm.Solver(s, prec=args.prec, stream=stream)
+    sv = rlbm.Solver(s, prec=args.prec, stream=stream, tune_cache=args.tune_cache)
+    # L2 flush before every timed step: write one buffer larger than L2, then
+    # read another one, so that the dirty lines the write leaves are written
+    # back before the step starts (the step neither finds its inputs in L2 nor
+    # pays for the flush buffer's write-backs)
     flush = torch.empty(max(2 * L2_BYTES, 256 << 20), dtype=torch.uint8, device="cuda")
+    evict = torch.ones(max(2 * L2_BYTES, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    sink = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        flush.zero_()
+        torch.sum(evict, dim=0, out=sink)
     with torch.cuda.stream(stream):
         sv.init(0)
     shape = sv.autotune()
@@ -248,7 +261,7 @@ def gpu_arm(args, rank, world, cpu_line):
     with torch.cuda.stream(stream):
         sv.init(0)
         for _ in range(args.warmup):
-            flush.zero_()
+            flush_l2()
             sv.step(1)
     sync_all()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -259,7 +272,7 @@ def gpu_arm(args, rank, world, cpu_line):
     sync_all()
     with torch.cuda.stream(stream):
         for k in range(args.steps):
-            flush.zero_()
+            flush_l2()
             ev[k][0].record(stream)
             sv.step(1)
             ev[k][1].record(stream)
@@ -305,8 +318,9 @@ def gpu_arm(args, rank, world, cpu_line):
         "config": {"workload": WORKLOAD, "precision": args.prec, "sites": sites,
                    "launch_shape": {"sites_per_block": shape[0] or 128,
                                     "blocks": shape[1] or "one per tile",
-                                    "kernel": "single-sample" if shape[0] == 0 else "batched"},
-                   "l2": "buffer of 2x L2 written before every timed step; steps timed alone",
+                                    "kernel": "single-sample" if shape[0] == 0 else
+                                              ("batched, staged pulls" if shape[2] else "batched")},
+                   "l2": "before every timed step a 2x L2 buffer is written, then another 2x L2 buffer read (cold L2, no pending write-backs); steps timed alone",
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": ncu_traffic(args.prec),
@@ -344,7 +358,8 @@ def ensemble_arm(args, rank, world):
     shard = [samples[i] for i in mine]
     sites = sum(x.sites for x in shard)
     stream = torch.cuda.Stream()
-    sv = rlbm.Solver(shard, prec=args.prec, stream=stream, graph_steps=10)
+    sv = rlbm.Solver(shard, prec=args.prec, stream=stream, graph_steps=10,
+                     tune_cache=args.tune_cache)
     with torch.cuda.stream(stream):
         for i in range(len(shard)):
             sv.init(i)
@@ -397,7 +412,8 @@ def ensemble_arm(args, rank, world):
         "config": {"workload": f"ensemble of {args.ensemble_size} uneven samples (seed 1234 + i), "
                                f"{total_sites} sites, sharded by sample",
                    "precision": args.prec, "sites_rank0": sites,
-                   "launch_shape": {"sites_per_block": shape[0] or 128, "blocks": shape[1] or "one per tile"},
+                   "launch_shape": {"sites_per_block": shape[0] or 128, "blocks": shape[1] or "one per tile",
+                                    "staged_pulls": bool(shape[2])},
                    "l2": "working set far larger than L2; steps back to back (CUDA graphs of 10)",
                    "parallelism": f"sample sharding over {world} rank(s)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

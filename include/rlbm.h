@@ -140,12 +140,27 @@ int rlbm_step(rlbm_ctx* ctx, int nsteps, double* residual);
 int rlbm_sample_residuals(const rlbm_ctx* ctx, double* out);
 
 /* Chooses the launch shape of the step kernel by timing the candidates on
- * the current state (without advancing it): sites per block (64 / 128 / 256)
- * and the number of blocks walking the work list of all samples (one per
- * tile, or 1..16 per SM, persistent).  With rlbm_config.tune_cache the
- * choice is read from / appended to that file.  Needs an initialised state.
- * Writes the choice to *bx and *grid (may be NULL). */
-int rlbm_autotune(rlbm_ctx* ctx, int* bx, int* grid);
+ * the current state (without advancing it): sites per block (64 / 128 / 256),
+ * the number of blocks walking the work list of all samples (one per tile, or
+ * 1..16 per SM, persistent) and whether the pulls are staged in shared memory
+ * (0 none; 1 bulk asynchronous copies of the 12 shifted row segments of a
+ * tile, the next tile in flight while the current one is computed).  With
+ * rlbm_config.tune_cache the choice is read from / appended to that file
+ * (one line "key bx grid staged").  Needs an initialised state.  Writes the
+ * choice to *bx, *grid and *staged (each may be NULL).  The staged kernels
+ * bound every wait (about 1 s); a wait that gives up raises the error bit
+ * that rlbm_check reports as RLBM_ETIMEOUT. */
+int rlbm_autotune(rlbm_ctx* ctx, int* bx, int* grid, int* staged);
+
+/* Sets the launch shape directly (same meaning as the rlbm_autotune outputs):
+ * bx 0 (single-sample kernel, one launch per sample; grid and staged must be
+ * 0) or 64 / 128 / 256 with grid >= 0 (0: one block per tile) and staged
+ * 0 (pulls straight from HBM) or 1 (the 12 row segments of a tile staged in
+ * shared memory by bulk asynchronous copies, next tile in flight).
+ * RLBM_EINVAL for any other combination.
+ * Every shape runs the same per-site arithmetic (results agree to the last
+ * bits; the code generator may contract multiply-adds differently per kernel). */
+int rlbm_set_launch_shape(rlbm_ctx* ctx, int bx, int grid, int staged);
 
 /* Macroscopic fields (n, u_x, u_y, T) of `sample` at the current time: the
  * Landau-frame values of the streamed populations, i.e. those the next

@@ -117,8 +117,10 @@ struct rlbm_ctx {
   double* host_pinned;        // residual accumulators + error word staging
   std::string err;
   // launch shape: bx = 0 runs the single-sample kernel per sample; bx = 64 /
-  // 128 / 256 runs the batched kernel over all samples with `grid` blocks
+  // 128 / 256 runs the batched kernel over all samples with `grid` blocks,
+  // with pulls staged in shared memory by bulk copies if `staged` is 1
   int bx, grid;
+  int staged;
   int graph_steps;
   std::string tune_cache;
   cudaGraphExec_t graph[2];   // graph_steps steps starting from buffer 0 / 1
@@ -143,6 +145,14 @@ int fail(rlbm_ctx* c, int code, const char* fmt, ...) {
 
 int cuda_fail(rlbm_ctx* c, cudaError_t e, const char* what) {
   return fail(c, RLBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Error code of a non-zero device error word (a timed-out wait outranks the
+// physics bits: the step it interrupted is incomplete).
+int error_word_fail(rlbm_ctx* c, unsigned bits) {
+  return fail(c, (bits & kErrTimeout) ? RLBM_ETIMEOUT : RLBM_ENAN,
+              "device error word 0x%x (1 non-finite, 2 unphysical, 4 no convergence, "
+              "8 wait timed out)", bits);
 }
 
 // Computes the layout of cfg; fills `out` when non-null.  Returns total bytes.
@@ -332,7 +342,7 @@ int upload_tables(rlbm_ctx* c) {
 }
 
 // Launches one time step reading buffer `from` (0 / 1) with the shape (bx, grid).
-cudaError_t launch_step(rlbm_ctx* c, int from, int res, int bx, int grid) {
+cudaError_t launch_step(rlbm_ctx* c, int from, int res, int bx, int grid, int staged) {
   double* acc = at<double>(c, c->acc_off);
   unsigned* err = at<unsigned>(c, c->err_off);
   void* uprev = c->ws + c->uprev_off;
@@ -357,14 +367,14 @@ cudaError_t launch_step(rlbm_ctx* c, int from, int res, int bx, int grid) {
   a.ntiles = c->ntiles[b];
   const int g = grid > 0 ? grid : (int)std::min<long long>(a.ntiles, 1LL << 30);
   cudaError_t e = c->ops->step_batch(c->ws, a, c->ws + c->ghost_off, c->force_any, res, bx, g,
-                                     uprev, acc, err, c->stream);
+                                     staged, uprev, acc, err, c->stream);
   if (e == cudaSuccess) c->launches++;
   return e;
 }
 
 // One time step of the context with its current shape; advances the parity.
 int advance(rlbm_ctx* c, int res) {
-  cudaError_t e = launch_step(c, c->cur, res, c->bx, c->grid);
+  cudaError_t e = launch_step(c, c->cur, res, c->bx, c->grid, c->staged);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
   c->cur ^= 1;
   c->steps++;
@@ -514,6 +524,7 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out) {
   if (r) { std::string m = c->err; rlbm_destroy(c); return fail(nullptr, r, "%s", m.c_str()); }
   c->bx = c->samples.size() == 1 ? 0 : 128;
   c->grid = c->samples.size() == 1 ? 0 : (int)std::min<long long>(c->ntiles[1], 1LL << 30);
+  c->staged = 0;
   *out = c;
   return RLBM_OK;
 }
@@ -624,7 +635,7 @@ int rlbm_step(rlbm_ctx* c, int nsteps, double* residual) {
     std::memcpy(&bits, c->host_pinned + 2 * ns, sizeof bits);
     if (bits) {
       cudaMemsetAsync(err, 0, sizeof(unsigned), c->stream);
-      return fail(c, RLBM_ENAN, "device error word 0x%x (1 non-finite, 2 unphysical, 4 no convergence)", bits);
+      return error_word_fail(c, bits);
     }
   }
   return RLBM_OK;
@@ -636,7 +647,27 @@ int rlbm_sample_residuals(const rlbm_ctx* c, double* out) {
   return RLBM_OK;
 }
 
-int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out) {
+namespace {
+bool valid_shape(int bx, int grid, int staged) {
+  if (bx != 0 && bx != 64 && bx != 128 && bx != 256) return false;
+  if (grid < 0 || staged < 0 || staged > 1) return false;
+  return !(bx == 0 && (grid != 0 || staged));
+}
+}  // namespace
+
+int rlbm_set_launch_shape(rlbm_ctx* c, int bx, int grid, int staged) {
+  if (!c) return RLBM_EINVAL;
+  if (!valid_shape(bx, grid, staged))
+    return fail(c, RLBM_EINVAL, "launch shape (bx %d, grid %d, staged %d) not supported", bx, grid,
+                staged);
+  c->bx = bx;
+  c->grid = grid;
+  c->staged = staged;
+  drop_graphs(c);
+  return RLBM_OK;
+}
+
+int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out, int* staged_out) {
   if (!c) return RLBM_EINVAL;
   if (!c->initialised) return fail(c, RLBM_ESTATE, "rlbm_init or rlbm_set_state first");
   const std::string key = tune_key(c);
@@ -646,11 +677,12 @@ int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out) {
       char line[768];
       while (fgets(line, sizeof line, f)) {
         char k[640];
-        int bx, grid;
-        if (sscanf(line, "%639s %d %d", k, &bx, &grid) == 3 && key == k &&
-            (bx == 0 || bx == 64 || bx == 128 || bx == 256) && grid >= 0) {
+        int bx, grid, staged = 0;
+        const int got = sscanf(line, "%639s %d %d %d", k, &bx, &grid, &staged);
+        if (got >= 3 && key == k && valid_shape(bx, grid, staged)) {
           c->bx = bx;
           c->grid = grid;
+          c->staged = staged;
           found = true;
         }
       }
@@ -658,30 +690,37 @@ int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out) {
     }
   }
   if (!found) {
-    struct Cand { int bx, grid; };
+    struct Cand { int bx, grid, staged; };
     std::vector<Cand> cands;
-    if (c->samples.size() == 1) cands.push_back({0, 0});
+    if (c->samples.size() == 1) cands.push_back({0, 0, 0});
     for (int b = 0; b < 3; ++b) {
       const int bx = kBxChoices[b];
-      cands.push_back({bx, 0});                       // one block per tile
+      cands.push_back({bx, 0, 0});                    // one block per tile
       for (int m : {1, 2, 4, 8, 16}) {
         const long long g = (long long)m * c->sm_count * (256 / bx);
-        if (g < c->ntiles[b]) cands.push_back({bx, (int)g});
+        if (g < c->ntiles[b]) cands.push_back({bx, (int)g, 0});
+      }
+      // staged pulls pay off when a block walks several tiles (prefetch)
+      for (int m : {1, 2, 4}) {
+        const long long g = (long long)m * c->sm_count * (256 / bx);
+        if (2 * g <= c->ntiles[b]) cands.push_back({bx, (int)g, 1});
       }
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    Cand pick = {c->bx, c->grid};
+    Cand pick = {c->bx, c->grid, c->staged};
     const long long launches = c->launches;
     for (const Cand& k : cands) {
       // repeated steps from the same input buffer: the state does not advance
       cudaError_t e = cudaSuccess;
-      for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_step(c, c->cur, 0, k.bx, k.grid);
+      for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+        e = launch_step(c, c->cur, 0, k.bx, k.grid, k.staged);
       cudaEventRecord(e0, c->stream);
       const int reps = 5;
-      for (int w = 0; w < reps && e == cudaSuccess; ++w) e = launch_step(c, c->cur, 0, k.bx, k.grid);
+      for (int w = 0; w < reps && e == cudaSuccess; ++w)
+        e = launch_step(c, c->cur, 0, k.bx, k.grid, k.staged);
       cudaEventRecord(e1, c->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e != cudaSuccess) {
@@ -698,9 +737,10 @@ int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out) {
     c->launches = launches;
     c->bx = pick.bx;
     c->grid = pick.grid;
+    c->staged = pick.staged;
     if (!c->tune_cache.empty()) {
       if (FILE* f = fopen(c->tune_cache.c_str(), "a")) {
-        fprintf(f, "%s %d %d\n", key.c_str(), c->bx, c->grid);
+        fprintf(f, "%s %d %d %d\n", key.c_str(), c->bx, c->grid, c->staged);
         fclose(f);
       }
     }
@@ -708,6 +748,7 @@ int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out) {
   drop_graphs(c);
   if (bx_out) *bx_out = c->bx;
   if (grid_out) *grid_out = c->grid;
+  if (staged_out) *staged_out = c->staged;
   return RLBM_OK;
 }
 
@@ -722,7 +763,7 @@ int rlbm_check(rlbm_ctx* c) {
   std::memcpy(&bits, c->host_pinned, sizeof bits);
   if (bits) {
     cudaMemsetAsync(err, 0, sizeof(unsigned), c->stream);
-    return fail(c, RLBM_ENAN, "device error word 0x%x (1 non-finite, 2 unphysical, 4 no convergence)", bits);
+    return error_word_fail(c, bits);
   }
   return RLBM_OK;
 }

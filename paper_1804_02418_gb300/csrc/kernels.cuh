@@ -14,6 +14,8 @@
 // coalesced), applies the boundary rules, collides in registers and writes 12
 // vectors of its own site into the other buffer.
 #pragma once
+#include <type_traits>
+
 #include "site.cuh"
 
 namespace rlbm {
@@ -78,6 +80,199 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, const DevSample&
   }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory staging of the pull.  For one tile (a row segment of BX sites
+// starting at x0 in row y) the 12 arriving populations come from 12 row
+// segments, one per direction plane: plane d, row y - dy_d, columns
+// x0 - dx_d .. x0 - dx_d + BX - 1.  Each segment is contiguous in HBM (whole
+// site vectors), so the persistent batched kernel moves it with one bulk
+// asynchronous copy (cp.async.bulk, completion counted in bytes on an
+// mbarrier) into a shared-memory slot row while the block still computes the
+// previous tile.  Columns outside the sample are clipped (their sites take the
+// boundary rules, as in pull()); a segment that wraps around a periodic x edge
+// is not staged and read directly.  Copies move whole 16-byte granules:
+// 16-bit storage (8-byte vectors) rounds a segment out to even sites, and the
+// slot index of column c is c - (a & ~(G - 1)), a = x0 - dx_d, G sites per
+// granule.
+// ---------------------------------------------------------------------------
+// Parking of the gathered populations (FP32 arithmetic).  After the moments
+// are formed, the 48 values of a site leave the registers for a shared-memory
+// area laid out [direction][thread] (16 bytes per entry: conflict-free) and
+// come back one direction pair at a time for the relaxation.  This frees
+// about 40 registers per thread, so more warps are resident to hide the
+// latency of the long per-site arithmetic.  The accesses are volatile so that
+// the compiler cannot keep the register copies alive instead.
+template <typename R> struct Park { static constexpr bool kOn = false; };
+template <> struct Park<float> { static constexpr bool kOn = true; };
+
+// Bytes of the parking area of a block of `threads` threads.
+template <typename R>
+__host__ __device__ constexpr size_t park_bytes(int threads) {
+  return Park<R>::kOn ? (size_t)kDirs * threads * 16 : 0;
+}
+
+__device__ __forceinline__ void park_store(uint32_t a, const float* v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n"
+               :: "r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]) : "memory");
+}
+__device__ __forceinline__ void park_load(uint32_t a, float* v) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a) : "memory");
+}
+
+// Control block after the two buffers: full[2] (mbarriers, 8 B each),
+// released[2] (+ pad), tiles[2] (int4), masks[2], abort flag (+ pad).
+constexpr size_t kStageCtlBytes = 16 + 16 + 32 + 8 + 8;
+
+template <typename S>
+struct Stage {
+  static constexpr int kVecBytes = 4 * (int)sizeof(S);
+  static constexpr int kG = kVecBytes >= 16 ? 1 : 16 / kVecBytes;   // sites per granule
+  template <int BX> __host__ __device__ static constexpr int slots() { return BX + 2 * (kG - 1); }
+  // elements of one buffer (12 slot rows)
+  template <int BX> __host__ __device__ static constexpr int buf_elems() { return kDirs * slots<BX>() * 4; }
+  // dynamic shared memory of the kernel: two buffers, then the control block
+  template <int BX> __host__ __device__ static constexpr size_t smem_bytes() {
+    return 2 * (size_t)buf_elems<BX>() * sizeof(S) + kStageCtlBytes +
+           park_bytes<typename Codec<S>::R>(BX);
+  }
+};
+
+constexpr long long kStageSpinCycles = 2000000000LL;   // about 1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+
+__device__ __forceinline__ void stage_bar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar), "r"(count) : "memory");
+}
+
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kStageSpinCycles) return false;
+  }
+}
+
+// Issued by the 32 lanes of one warp (lane d < 12 copies direction d): the
+// segments of tile (x0, y) of sample s into `buf`; *mask gets bit d for every
+// staged direction and *tile the tile (sample, x0, y).  One arrive with the
+// expected byte count (release semantics: mask and tile become visible to the
+// waiting threads) completes the phase together with the copies.
+template <typename S, int BX>
+__device__ __forceinline__ void stage_issue(const S* __restrict__ fin, const DevSample& s, int x0,
+                                            int y, S* buf, uint32_t bar, unsigned* mask,
+                                            int4* tile, int sample) {
+  constexpr int G = Stage<S>::kG, VB = Stage<S>::kVecBytes, SL = Stage<S>::template slots<BX>();
+  const int lane = threadIdx.x & 31;
+  const int nv = min(BX, s.nx - x0);
+  bool ok = false;
+  uint32_t bytes = 0, dst = 0;
+  const S* src = nullptr;
+  if (lane < kDirs) {
+    const int d = lane, dx = hop_x(d), dy = hop_y(d);
+    int sy = y - dy;
+    if (s.periodic_y) sy = sy < 0 ? sy + s.ny : (sy >= s.ny ? sy - s.ny : sy);
+    if ((unsigned)sy < (unsigned)s.ny) {
+      const int a = x0 - dx;
+      int lo = a, hi = a + nv;
+      const bool wraps = s.periodic_x && (lo < 0 || hi > s.nx);
+      if (!s.periodic_x) { lo = max(lo, 0); hi = min(hi, s.nx); }
+      if (!wraps && lo < hi) {
+        const int lor = lo & ~(G - 1), hir = (hi + G - 1) & ~(G - 1);
+        ok = true;
+        bytes = (uint32_t)(hir - lor) * VB;
+        src = fin + vec_index(s, d, (long long)sy * s.ldx + lor);
+        dst = smem_addr(buf + ((long long)d * SL + (lor - (a & ~(G - 1)))) * 4);
+      }
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, ok);
+  uint32_t total = bytes;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+  if (lane == 0) {
+    *mask = m;
+    *tile = make_int4(sample, x0, y, 0);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                 :: "r"(bar), "r"(total) : "memory");
+  }
+  __syncwarp();
+  if (ok)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+        :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Where the 48 arriving deviations of a site come from: straight from HBM, or
+// from the staged slot rows of its tile.
+struct DirectSrc {};
+template <typename S, int BX>
+struct StagedSrc {
+  uint32_t buf;     // shared-window address of the tile's slot rows
+  unsigned mask;    // bit d: direction d staged
+  int x0;           // first column of the tile
+};
+
+// pull() with staged segments: a source inside the sample whose direction is
+// staged is read from shared memory; everything else as in pull().
+template <typename S, bool INTERIOR, int BX, class C>
+__device__ __forceinline__ void pull_staged(const S* __restrict__ fin, const DevSample& s, int x,
+                                            int y, const typename Codec<S>::R* __restrict__ ghost,
+                                            const C& qc, const StagedSrc<S, BX>& st,
+                                            typename Codec<S>::R (&f)[kQ]) {
+  constexpr int G = Stage<S>::kG, SL = Stage<S>::template slots<BX>();
+  constexpr int VB = Stage<S>::kVecBytes;
+  const long long site = (long long)y * s.ldx + x;
+  const int i = x - st.x0;
+  if (INTERIOR && __builtin_expect(st.mask == (1u << kDirs) - 1u, 1)) {
+#pragma unroll
+    for (int d = 0; d < kDirs; ++d)
+      Codec<S>::load4s(st.buf + (uint32_t)((d * SL + i + ((st.x0 - hop_x(d)) & (G - 1))) * VB),
+                       dir_kind(d), qc, &f[4 * d]);
+    return;
+  }
+#pragma unroll
+  for (int d = 0; d < kDirs; ++d) {
+    const int dx = hop_x(d), dy = hop_y(d);
+    const bool staged = (st.mask >> d) & 1u;
+    const uint32_t sp = st.buf + (uint32_t)((d * SL + i + ((st.x0 - dx) & (G - 1))) * VB);
+    if (INTERIOR) {
+      if (staged) Codec<S>::load4s(sp, dir_kind(d), qc, &f[4 * d]);
+      else Codec<S>::load4(fin + vec_index(s, d, site - ((long long)dy * s.ldx + dx)), dir_kind(d),
+                           qc, &f[4 * d]);
+    } else {
+      int sx = x - dx, sy = y - dy;
+      if (s.periodic_x) sx = sx < 0 ? sx + s.nx : (sx >= s.nx ? sx - s.nx : sx);
+      if (s.periodic_y) sy = sy < 0 ? sy + s.ny : (sy >= s.ny ? sy - s.ny : sy);
+      const bool inside = (unsigned)sx < (unsigned)s.nx && (unsigned)sy < (unsigned)s.ny;
+      if (inside) {
+        if (staged) Codec<S>::load4s(sp, dir_kind(d), qc, &f[4 * d]);
+        else Codec<S>::load4(fin + vec_index(s, d, (long long)sy * s.ldx + sx), dir_kind(d), qc,
+                             &f[4 * d]);
+      } else {
+        const int owner = contact_of(s, sx, sy);
+        if (owner >= 0) {
+#pragma unroll
+          for (int j = 0; j < kShells; ++j) f[4 * d + j] = ghost[owner * kQ + 4 * d + j];
+        } else {
+          Codec<S>::load4(fin + vec_index(s, d ^ 1, site), dir_kind(d), qc, &f[4 * d]);
+        }
+      }
+    }
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void block_reduce_add2(double a, double b, double* acc) {
   __shared__ double sa[32], sb[32];
@@ -102,6 +297,19 @@ __device__ __forceinline__ void block_reduce_add2(double a, double b, double* ac
       atomicAdd(acc, a);
       atomicAdd(acc + 1, b);
     }
+  }
+}
+
+// Warp sums of (a, b) added to acc[0], acc[1] by lane 0 (no block barrier).
+__device__ __forceinline__ void warp_reduce_add2(double a, double b, double* acc) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, a);
+    atomicAdd(acc + 1, b);
   }
 }
 
@@ -130,16 +338,36 @@ __device__ __forceinline__ void balance(const R* in, const R* out, const C& qc, 
   }
 }
 
-// Fused stream + collide of site (x, y) (nothing if x >= nx).  RES: 0 nothing
-// extra; 1 store u for the residual; 2 add |u - u_prev|^2 and |u|^2 to
-// r_du2, r_u2 (the caller reduces them).  All 32 threads of a warp must hold
-// consecutive x of the same row (the interior test is per warp).
+// Gathers the 48 deviations streamed into site (x < nx, y): from HBM or from
+// the staged slot rows.  All 32 threads of a warp must hold consecutive x of
+// the same row (the interior test is per warp).
+template <typename S, class C, class SRC>
+__device__ __forceinline__ void gather(const S* __restrict__ fin, const DevSample& s, int x, int y,
+                                       const typename Codec<S>::R* __restrict__ ghost, const C& qc,
+                                       const SRC& src, typename Codec<S>::R (&f)[kQ]) {
+  // warp-uniform: the 32 sites of this warp pull only from inside the rectangle
+  const int wx0 = x & ~31;
+  const bool interior = wx0 >= kRadius && wx0 + 32 + kRadius <= s.nx &&
+                        y >= kRadius && y + kRadius < s.ny;
+  if constexpr (std::is_same<SRC, DirectSrc>::value) {
+    if (interior) pull<S, true>(fin, s, x, y, ghost, qc, f);
+    else          pull<S, false>(fin, s, x, y, ghost, qc, f);
+  } else {
+    if (interior) pull_staged<S, true>(fin, s, x, y, ghost, qc, src, f);
+    else          pull_staged<S, false>(fin, s, x, y, ghost, qc, src, f);
+  }
+}
+
+// Collision of the gathered deviations f of site (x < nx, y) and store of the
+// 48 new deviations into fout.  RES: 0 nothing extra; 1 store u for the
+// residual; 2 add |u - u_prev|^2 and |u|^2 to r_du2, r_u2 (the caller
+// reduces them).
 template <typename S, bool FORCE, int RES, class C>
-__device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restrict__ fout,
-                                          const DevSample& s, int x, int y,
-                                          const typename Codec<S>::R* __restrict__ ghost,
-                                          const StepAux<typename Codec<S>::R>& aux, const C& qc,
-                                          double& r_du2, double& r_u2) {
+__device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* __restrict__ fout,
+                                              const DevSample& s, int x, int y,
+                                              const StepAux<typename Codec<S>::R>& aux,
+                                              const C& qc, double& r_du2, double& r_u2,
+                                              uint32_t park) {
   using R = typename Codec<S>::R;
   // FP32 storage: the FP32 quadrature constants satisfy Eq. orthonormal only
   // to ~1e-7, which would break the exact conservation of N^0 and T^0a by the
@@ -148,16 +376,14 @@ __device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restri
   //   sum_i p0 (f* - f) = 0,  sum_i p0 p^a (f* - f) = (F.N_E, F N_E^0)
   // by a correction on the (5,0)-type directions (solved with the constants P**, px).
   constexpr bool kProject = sizeof(S) == sizeof(float);
-  if (x < s.nx) {
-    R f[kQ];
-    // warp-uniform: the 32 sites of this warp pull only from inside the rectangle
-    const int wx0 = x & ~31;
-    const bool interior = wx0 >= kRadius && wx0 + 32 + kRadius <= s.nx &&
-                          y >= kRadius && y + kRadius < s.ny;
-    if (interior) pull<S, true>(fin, s, x, y, ghost, qc, f);
-    else          pull<S, false>(fin, s, x, y, ghost, qc, f);
-
+  {
     const Moments<R> m = moments(f, qc);
+    // park: entry of direction d at park + d * blockDim.x * 16
+    const uint32_t park_stride = blockDim.x * 16u;
+    if constexpr (Park<R>::kOn) {
+#pragma unroll
+      for (int d = 0; d < kDirs; ++d) park_store(park + d * park_stride, &f[4 * d]);
+    }
     Macro<R> M;
     const bool conv = landau(m, M);
     unsigned bad = 0;
@@ -183,6 +409,10 @@ __device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restri
       R Rp[4], Rn[4], omp, omn;
       pair_cubics<R, FORCE>(d, c, nT, nmT, gt, gux, guy, Fx, Fy, Rp, Rn, omp, omn);
       const int kind = dir_kind(d);
+      if constexpr (Park<R>::kOn) {
+        park_load(park + d * park_stride, &f[4 * d]);
+        park_load(park + (d + 1) * park_stride, &f[4 * d + 4]);
+      }
       if (kProject) {
         R in[8];
 #pragma unroll
@@ -242,15 +472,30 @@ __device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restri
   }
 }
 
+// Fused stream + collide of site (x, y) (nothing if x >= nx).
+template <typename S, bool FORCE, int RES, class C>
+__device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restrict__ fout,
+                                          const DevSample& s, int x, int y,
+                                          const typename Codec<S>::R* __restrict__ ghost,
+                                          const StepAux<typename Codec<S>::R>& aux, const C& qc,
+                                          double& r_du2, double& r_u2, uint32_t park) {
+  if (x < s.nx) {
+    typename Codec<S>::R f[kQ];
+    gather(fin, s, x, y, ghost, qc, DirectSrc(), f);
+    collide_store<S, FORCE, RES>(f, fout, s, x, y, aux, qc, r_du2, r_u2, park);
+  }
+}
+
 // One sample, one block row of kBX sites.
 template <typename S, bool FORCE, int RES, class C>
 __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restrict__ fout,
                                           const DevSample& s,
                                           const typename Codec<S>::R* __restrict__ ghost,
-                                          const StepAux<typename Codec<S>::R>& aux, const C& qc) {
+                                          const StepAux<typename Codec<S>::R>& aux, const C& qc,
+                                          unsigned char* park) {
   double r_du2 = 0.0, r_u2 = 0.0;
   site_step<S, FORCE, RES>(fin, fout, s, blockIdx.x * kBX + threadIdx.x, blockIdx.y, ghost, aux,
-                           qc, r_du2, r_u2);
+                           qc, r_du2, r_u2, smem_addr(park) + threadIdx.x * 16u);
   if (RES == 2) block_reduce_add2<typename Codec<S>::R>(r_du2, r_u2, aux.acc);
 }
 
@@ -271,7 +516,10 @@ struct BatchArgs {
 template <typename S, bool FORCE, int RES, int BX, class C>
 __device__ __forceinline__ void batch_body(S* __restrict__ base, const BatchArgs& b,
                                            const typename Codec<S>::R* __restrict__ ghost,
-                                           const StepAux<typename Codec<S>::R>& aux, const C& qc) {
+                                           const StepAux<typename Codec<S>::R>& aux, const C& qc,
+                                           unsigned char* park) {
+  const uint32_t my_park = smem_addr(park) + threadIdx.x * 16u;
+#pragma unroll 1
   for (long long t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
     int lo = 0, hi = b.nsamples;                 // tile_start[lo] <= t < tile_start[hi]
     while (hi - lo > 1) {
@@ -287,12 +535,128 @@ __device__ __forceinline__ void batch_body(S* __restrict__ base, const BatchArgs
     const long long oout = b.cur ? s.off[0] : s.off[1];
     double r_du2 = 0.0, r_u2 = 0.0;
     site_step<S, FORCE, RES>(base + oin, base + oout, s, x, y,
-                             ghost + (long long)lo * kMaxContacts * kQ, aux, qc, r_du2, r_u2);
+                             ghost + (long long)lo * kMaxContacts * kQ, aux, qc, r_du2, r_u2,
+                             my_park);
     // per-sample residual accumulators: acc[2 k], acc[2 k + 1]
     if (RES == 2) {
       block_reduce_add2<typename Codec<S>::R>(r_du2, r_u2, aux.acc + 2 * lo);
       __syncthreads();   // the reduction's shared scratch is reused by the next tile
     }
+  }
+}
+
+// The batched step with staged pulls (persistent: gridDim.x blocks walk the
+// tile list with a grid stride; the block's k-th tile is blockIdx.x + k G,
+// G = gridDim.x).  Two slot-row buffers alternate: buffer b holds tiles
+// k = b, b + 2, ... (use j = k / 2), and mbarrier full[b] completes phase j
+// when tile 2 j + b has landed (one arrive with the byte count by the issuing
+// warp, plus the copies' bytes).  Warp 0 fills both buffers up front; after
+// that the last warp to finish gathering tile k (a shared counter per buffer)
+// issues tile k + 2 into the buffer it just freed, so two tiles are always in
+// flight or landed and no warp waits for another one.  Every wait is bounded
+// (about 1 s): a warp that gives up sets kErrTimeout and a shared abort flag,
+// waits once more (bounded) for the copies of both buffers, and leaves the
+// loop; the other warps leave at their next tile.
+template <typename S, bool FORCE, int RES, int BX, class C>
+__device__ __forceinline__ void staged_batch_body(S* __restrict__ base, const BatchArgs& b,
+                                                  const typename Codec<S>::R* __restrict__ ghost,
+                                                  const StepAux<typename Codec<S>::R>& aux,
+                                                  const C& qc, unsigned char* smem) {
+  using R = typename Codec<S>::R;
+  constexpr int BUF = Stage<S>::template buf_elems<BX>();
+  constexpr int kWarps = BX / 32;
+  S* stage = reinterpret_cast<S*>(smem);
+  unsigned char* ctl = smem + 2 * (size_t)BUF * sizeof(S);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ctl);          // [2]
+  unsigned* released = reinterpret_cast<unsigned*>(ctl + 16);  // [2] warps done gathering
+  int4* tiles = reinterpret_cast<int4*>(ctl + 32);             // [2]: sample, x0, y
+  unsigned* masks = reinterpret_cast<unsigned*>(ctl + 64);     // [2]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctl + 72);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t my_park = smem_addr(ctl + kStageCtlBytes) + tid * 16u;
+  const uint32_t full0 = smem_addr(&full[0]), full1 = smem_addr(&full[1]);
+  const uint32_t buf0 = smem_addr(stage), buf1 = smem_addr(stage + BUF);
+  auto full_bar = [&](int k) { return k ? full1 : full0; };
+  const long long G = gridDim.x;
+  long long t = blockIdx.x;
+  if (t >= b.ntiles) return;
+  if (tid == 0) {
+    stage_bar_init(full0, 1);
+    stage_bar_init(full1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    released[0] = released[1] = 0;
+    *abort_flag = 0;
+  }
+  __syncthreads();
+
+  // fills buffer `buf` with tile tt (all lanes of the calling warp)
+  auto issue = [&](long long tt, int buf) {
+    int lo = 0, hi = b.nsamples;                 // tile_start[lo] <= tt < tile_start[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(b.tile_start + mid) <= tt) lo = mid; else hi = mid;
+    }
+    const DevSample& s = b.samples[lo];
+    const long long lt = tt - __ldg(b.tile_start + lo);
+    const int tpr = (s.nx + BX - 1) / BX;
+    const int y = (int)(lt / tpr);
+    const int x0 = (int)(lt - (long long)y * tpr) * BX;
+    const S* fin = base + (b.cur ? s.off[1] : s.off[0]);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    stage_issue<S, BX>(fin, s, x0, y, stage + (size_t)buf * BUF, full_bar(buf), &masks[buf],
+                       &tiles[buf], lo);
+  };
+
+  if (tid < 32) {
+    issue(t, 0);
+    if (t + G < b.ntiles) issue(t + G, 1);
+  }
+#pragma unroll 1
+  for (int it = 0;; ++it) {
+    const int cb = it & 1;
+    bool ok = !*abort_flag && stage_wait(full_bar(cb), (it >> 1) & 1);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) {
+      if (lane == 0 && !*abort_flag) {
+        *abort_flag = 1;
+        atomicOr(aux.err, kErrTimeout);
+      }
+      // copies that may still be in flight into either buffer
+      stage_wait(full_bar(cb), (it >> 1) & 1);
+      if (t + G < b.ntiles) stage_wait(full_bar(cb ^ 1), ((it + 1) >> 1) & 1);
+      break;
+    }
+    const int4 tl = tiles[cb];
+    const StagedSrc<S, BX> src{cb ? buf1 : buf0, masks[cb], tl.y};
+    const DevSample s = b.samples[tl.x];
+    const int x = tl.y + tid;
+    R f[kQ];
+    if (x < s.nx) gather(base + (b.cur ? s.off[1] : s.off[0]), s, x, tl.z,
+                         ghost + (long long)tl.x * kMaxContacts * kQ, qc, src, f);
+    __syncwarp();
+    // the last warp done with this buffer refills it with tile k + 2
+    if (t + 2 * G < b.ntiles) {
+      unsigned last = 0;
+      if (lane == 0) {
+        // a compiler barrier too: this tile's shared reads stay before it
+        unsigned prev;
+        asm volatile("atom.shared.add.u32 %0, [%1], 1;\n"
+                     : "=r"(prev) : "r"(smem_addr(&released[cb])) : "memory");
+        last = prev == kWarps - 1;
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) {
+        if (lane == 0) released[cb] = 0;
+        issue(t + 2 * G, cb);
+      }
+    }
+    double r_du2 = 0.0, r_u2 = 0.0;
+    if (x < s.nx)
+      collide_store<S, FORCE, RES>(f, base + (b.cur ? s.off[0] : s.off[1]), s, x, tl.z, aux, qc,
+                                   r_du2, r_u2, my_park);
+    if (RES == 2) warp_reduce_add2(r_du2, r_u2, aux.acc + 2 * tl.x);
+    t += G;
+    if (t >= b.ntiles) break;
   }
 }
 

@@ -16,9 +16,11 @@ struct PrecOps {
                       bool force, int res, void* uprev, double* acc, unsigned* err,
                       cudaStream_t st);
   // All samples in one launch over the tile list (bx: 64 / 128 / 256 sites per
-  // tile and block; grid: number of blocks walking the list).
+  // tile and block; grid: number of blocks walking the list; staged: 0 pulls
+  // straight from HBM, 1 the tile's row segments staged in shared memory by
+  // bulk copies).
   cudaError_t (*step_batch)(void* base, const BatchArgs& b, const void* ghost, bool force,
-                            int res, int bx, int grid, void* uprev, double* acc,
+                            int res, int bx, int grid, int staged, void* uprev, double* acc,
                             unsigned* err, cudaStream_t st);
   cudaError_t (*moments)(const void* fin, const DevSample& s, const void* ghost, double* n,
                          double* ux, double* uy, double* T, unsigned* err, cudaStream_t st);

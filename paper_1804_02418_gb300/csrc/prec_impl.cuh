@@ -14,24 +14,59 @@ using R = typename Codec<S>::R;
 
 __constant__ QuadConsts<R> c_qc;
 
-// RLBM_STEP_MIN_BLOCKS: resident blocks per SM the register allocation aims
-// for (measured per storage type: FP32 runs best at 4 blocks / 128
-// registers, 16-bit storage at 5 blocks).
+// RLBM_STEP_MIN_BLOCKS: resident blocks of 128 threads per SM the register
+// allocation aims for (measured per storage type: with the populations parked
+// in shared memory, FP32 arithmetic runs best at 5 blocks / 96 registers; the
+// FP64 kernels take all the registers they want).
 #ifndef RLBM_STEP_MIN_BLOCKS
 #define RLBM_STEP_MIN_BLOCKS 4
 #endif
+// Registers per thread of every step kernel of the module: one cap for all
+// block widths (64 / 128 / 256 sites), so that every launch shape compiles the
+// per-site arithmetic alike (the code generator's multiply-add contraction
+// depends on the register budget) and all shapes give bit-identical states.
+constexpr int kStepRegs = (65536 / (RLBM_STEP_MIN_BLOCKS * kBX)) > 255
+                              ? 255 : ((65536 / (RLBM_STEP_MIN_BLOCKS * kBX)) & ~7);
 
+// Dynamic shared memory of the direct step kernels: the parking area
+// (park_bytes: 12 x threads x 16 B with FP32 arithmetic, none with FP64).
 template <bool FORCE, int RES>
-__global__ void __launch_bounds__(kBX, RLBM_STEP_MIN_BLOCKS) k_step(const S* __restrict__ fin, S* __restrict__ fout,
+__global__ void __maxnreg__(kStepRegs) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                               DevSample s, const R* __restrict__ ghost,
                                               StepAux<R> aux) {
-  step_body<S, FORCE, RES>(fin, fout, s, ghost, aux, c_qc);
+  extern __shared__ __align__(128) unsigned char park_smem[];
+  step_body<S, FORCE, RES>(fin, fout, s, ghost, aux, c_qc, park_smem);
 }
 
 template <bool FORCE, int RES, int BX>
-__global__ void __launch_bounds__(BX, RLBM_STEP_MIN_BLOCKS * kBX / BX)
+__global__ void __maxnreg__(kStepRegs)
 k_step_batch(S* __restrict__ base, BatchArgs b, const R* __restrict__ ghost, StepAux<R> aux) {
-  batch_body<S, FORCE, RES, BX>(base, b, ghost, aux, c_qc);
+  extern __shared__ __align__(128) unsigned char park_smem[];
+  batch_body<S, FORCE, RES, BX>(base, b, ghost, aux, c_qc, park_smem);
+}
+
+// Staged pulls (persistent; dynamic shared memory: two slot-row buffers).
+template <bool FORCE, int RES, int BX>
+__global__ void __maxnreg__(kStepRegs)
+k_step_staged(S* __restrict__ base, BatchArgs b, const R* __restrict__ ghost, StepAux<R> aux) {
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  staged_batch_body<S, FORCE, RES, BX>(base, b, ghost, aux, c_qc, stage_smem);
+}
+
+template <int BX>
+cudaError_t allow_stage_smem() {
+  const int bytes = (int)Stage<S>::template smem_bytes<BX>();
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* fn) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  set((const void*)k_step_staged<true, 0, BX>);
+  set((const void*)k_step_staged<true, 1, BX>);
+  set((const void*)k_step_staged<true, 2, BX>);
+  set((const void*)k_step_staged<false, 0, BX>);
+  set((const void*)k_step_staged<false, 1, BX>);
+  set((const void*)k_step_staged<false, 2, BX>);
+  return e;
 }
 
 __global__ void __launch_bounds__(kBX) k_moments(const S* __restrict__ fin, DevSample s,
@@ -80,7 +115,12 @@ cudaError_t upload(const double p0[4], const double w[2][4], double scale) {
   h.P10 = R(4.0 * K[2] / det);
   h.P11 = R(-4.0 * K[1] / det);
   h.px = R(-1.0 / (2.0 * K[3]));
-  return cudaMemcpyToSymbol(c_qc, &h, sizeof(h));
+  cudaError_t e = cudaMemcpyToSymbol(c_qc, &h, sizeof(h));
+  // shared-memory opt-in of the staged kernels (current device)
+  if (e == cudaSuccess) e = allow_stage_smem<64>();
+  if (e == cudaSuccess) e = allow_stage_smem<128>();
+  if (e == cudaSuccess) e = allow_stage_smem<256>();
+  return e;
 }
 
 cudaError_t step(const void* fin, void* fout, const DevSample& s, const void* ghost, bool force,
@@ -90,41 +130,56 @@ cudaError_t step(const void* fin, void* fout, const DevSample& s, const void* gh
   S* b = static_cast<S*>(fout);
   const R* g = static_cast<const R*>(ghost);
   const dim3 grid = site_grid(s);
+  const size_t pk = park_bytes<R>(kBX);
   if (force) {
-    if (res == 0) k_step<true, 0><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
-    else if (res == 1) k_step<true, 1><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
-    else k_step<true, 2><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
+    if (res == 0) k_step<true, 0><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
+    else if (res == 1) k_step<true, 1><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
+    else k_step<true, 2><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
   } else {
-    if (res == 0) k_step<false, 0><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
-    else if (res == 1) k_step<false, 1><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
-    else k_step<false, 2><<<grid, kBX, 0, st>>>(a, b, s, g, aux);
+    if (res == 0) k_step<false, 0><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
+    else if (res == 1) k_step<false, 1><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
+    else k_step<false, 2><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
   }
   return cudaGetLastError();
 }
 
 template <int BX>
 void launch_batch(S* base, const BatchArgs& b, const R* g, bool force, int res, int grid,
-                  const StepAux<R>& aux, cudaStream_t st) {
+                  int staged, const StepAux<R>& aux, cudaStream_t st) {
+  if (staged == 1) {
+    const size_t sm = Stage<S>::template smem_bytes<BX>();
+    if (force) {
+      if (res == 0) k_step_staged<true, 0, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
+      else if (res == 1) k_step_staged<true, 1, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
+      else k_step_staged<true, 2, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
+    } else {
+      if (res == 0) k_step_staged<false, 0, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
+      else if (res == 1) k_step_staged<false, 1, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
+      else k_step_staged<false, 2, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
+    }
+    return;
+  }
+  const size_t pk = park_bytes<R>(BX);
   if (force) {
-    if (res == 0) k_step_batch<true, 0, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
-    else if (res == 1) k_step_batch<true, 1, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
-    else k_step_batch<true, 2, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
+    if (res == 0) k_step_batch<true, 0, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
+    else if (res == 1) k_step_batch<true, 1, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
+    else k_step_batch<true, 2, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
   } else {
-    if (res == 0) k_step_batch<false, 0, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
-    else if (res == 1) k_step_batch<false, 1, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
-    else k_step_batch<false, 2, BX><<<grid, BX, 0, st>>>(base, b, g, aux);
+    if (res == 0) k_step_batch<false, 0, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
+    else if (res == 1) k_step_batch<false, 1, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
+    else k_step_batch<false, 2, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
   }
 }
 
 cudaError_t step_batch(void* base, const BatchArgs& b, const void* ghost, bool force, int res,
-                       int bx, int grid, void* uprev, double* acc, unsigned* err,
+                       int bx, int grid, int staged, void* uprev, double* acc, unsigned* err,
                        cudaStream_t st) {
   StepAux<R> aux{static_cast<R*>(uprev), acc, err};
   S* p = static_cast<S*>(base);
   const R* g = static_cast<const R*>(ghost);
-  if (bx == 64) launch_batch<64>(p, b, g, force, res, grid, aux, st);
-  else if (bx == 256) launch_batch<256>(p, b, g, force, res, grid, aux, st);
-  else launch_batch<128>(p, b, g, force, res, grid, aux, st);
+  if (bx == 64) launch_batch<64>(p, b, g, force, res, grid, staged, aux, st);
+  else if (bx == 256) launch_batch<256>(p, b, g, force, res, grid, staged, aux, st);
+  else launch_batch<128>(p, b, g, force, res, grid, staged, aux, st);
   return cudaGetLastError();
 }
 

@@ -69,6 +69,7 @@ struct DevSample {
 constexpr unsigned kErrNonFinite = 1u;
 constexpr unsigned kErrUnphysical = 2u;
 constexpr unsigned kErrNoConvergence = 4u;
+constexpr unsigned kErrTimeout = 8u;      // a bounded wait inside a kernel gave up
 
 // ---------------------------------------------------------------------------
 // Storage codecs.  The four shells of one (direction, site) are stored side by
@@ -84,6 +85,12 @@ template <> struct Codec<double> {
     const double2 a = __ldg(reinterpret_cast<const double2*>(p));
     const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  // from shared memory (32-bit shared-window address)
+  template <class C>
+  __device__ static void load4s(uint32_t a, int, const C&, R* o) {
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(o[0]), "=d"(o[1]) : "r"(a));
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(o[2]), "=d"(o[3]) : "r"(a + 16));
   }
   template <class C>
   __device__ static void store4(double* p, int, const C&, const R* v) {
@@ -101,6 +108,11 @@ template <> struct Codec<float> {
     o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
   }
   template <class C>
+  __device__ static void load4s(uint32_t a, int, const C&, R* o) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]) : "r"(a));
+  }
+  template <class C>
   __device__ static void store4(float* p, int, const C&, const R* v) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   }
@@ -114,6 +126,15 @@ template <typename H> struct Codec16 {
   template <class C>
   __device__ static void load4(const H* p, int kind, const C& c, R* o) {
     const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    H h[4];
+    memcpy(h, &u, sizeof u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]) * c.dec[kind][j];
+  }
+  template <class C>
+  __device__ static void load4s(uint32_t a, int kind, const C& c, R* o) {
+    uint2 u;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];\n" : "=r"(u.x), "=r"(u.y) : "r"(a));
     H h[4];
     memcpy(h, &u, sizeof u);
 #pragma unroll

@@ -68,7 +68,9 @@ EXPORTS = {
     "rlbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "rlbm_sample_residuals": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "rlbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
-                                     ctypes.POINTER(ctypes.c_int)]),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "rlbm_set_launch_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int]),
     "rlbm_velocity_residual_static": (ctypes.c_int, [ctypes.c_void_p] * 4 + [
         ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -243,10 +245,16 @@ class Solver:
         return np.array(out[:])
 
     def autotune(self):
-        """Times the launch shapes on the current state; returns (bx, grid)."""
-        bx, grid = ctypes.c_int(), ctypes.c_int()
-        self._check(self.lib.rlbm_autotune(self.ctx, ctypes.byref(bx), ctypes.byref(grid)))
-        return bx.value, grid.value
+        """Times the launch shapes on the current state; returns (bx, grid, staged)."""
+        bx, grid, staged = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.rlbm_autotune(self.ctx, ctypes.byref(bx), ctypes.byref(grid),
+                                           ctypes.byref(staged)))
+        return bx.value, grid.value, staged.value
+
+    def set_launch_shape(self, bx, grid=0, staged=0):
+        """Pins the launch shape (bx 0: single-sample kernel; 64 / 128 / 256:
+        batched, grid blocks (0: one per tile), staged pulls if staged)."""
+        self._check(self.lib.rlbm_set_launch_shape(self.ctx, int(bx), int(grid), int(staged)))
 
     @property
     def steps_done(self) -> int:
