@@ -430,6 +430,10 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
         if (kind == 0) {
           Codec<S>::store4(fout + vec_index(s, d, site), kind, qc, &f[4 * d]);
           Codec<S>::store4(fout + vec_index(s, d + 1, site), kind, qc, &f[4 * d + 4]);
+        } else if constexpr (Park<R>::kOn) {
+          // (5,0)-type: wait for the correction in the parking area, not in registers
+          park_store(park + d * park_stride, &f[4 * d]);
+          park_store(park + (d + 1) * park_stride, &f[4 * d + 4]);
         }
       } else {
         relax_shells(Rp, omp, kind, qc, &f[4 * d]);
@@ -452,6 +456,7 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
 #pragma unroll
       for (int d = 8; d < kDirs; ++d) {
         const R cd = l1 + (hop_x(d) > 0 ? lx : hop_x(d) < 0 ? -lx : hop_y(d) > 0 ? ly : -ly);
+        if constexpr (Park<R>::kOn) park_load(park + d * park_stride, &f[4 * d]);
 #pragma unroll
         for (int j = 0; j < kShells; ++j)
           f[4 * d + j] = fma(qc.w[1][j], fma(qc.p0[j], cd, l0), f[4 * d + j]);

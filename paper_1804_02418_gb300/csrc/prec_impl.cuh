@@ -16,8 +16,9 @@ __constant__ QuadConsts<R> c_qc;
 
 // RLBM_STEP_MIN_BLOCKS: resident blocks of 128 threads per SM the register
 // allocation aims for (measured per storage type: with the populations parked
-// in shared memory, FP32 arithmetic runs best at 5 blocks / 96 registers; the
-// FP64 kernels take all the registers they want).
+// in shared memory, FP32 arithmetic runs best at 6 blocks / 80 registers, for
+// FP32 and 16-bit storage alike; the FP64 kernels take all the registers
+// they want).
 #ifndef RLBM_STEP_MIN_BLOCKS
 #define RLBM_STEP_MIN_BLOCKS 4
 #endif
