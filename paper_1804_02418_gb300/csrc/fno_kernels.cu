@@ -144,17 +144,31 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
 }
 
 // ---------------------------------------------------------------------------
-// Fifth-generation tensor-core GEMM (tcgen05 / TMEM), one CTA per 128 x 64
-// output tile.  Four warps stage K slabs of 64 into shared memory in the
-// canonical no-swizzle K-major layout (8 x 16-byte core matrices: the two
-// 8-element halves of a K16 step are LBO = 128 B apart, consecutive 8-row
-// groups SBO = 1024 B apart); one thread issues four tcgen05.mma (M = 128,
-// N = 64, K = 16, BF16 x BF16 -> FP32 in TMEM) per slab and commits them to
-// an mbarrier; the accumulator is read back with tcgen05.ld (warp w owns TMEM
-// lanes 32 w .. 32 w + 31 = output rows).  Every wait is bounded: on timeout
-// the CTA raises the error flag, skips its tile, frees its TMEM and returns.
+// Fifth-generation tensor-core GEMM (tcgen05 / TMEM): one CTA of 4 warps per
+// 128 x BN output tile (BN = 32 / 64 / 128 chosen per call), K in slabs of 64.
+//
+// Operands live in shared memory in the canonical no-swizzle K-major layout:
+// 8 x 16-byte core matrices (8 rows, 8 consecutive k each), the two k-halves
+// of a K16 step LBO = 128 B apart, consecutive 8-row groups SBO = 1040 B apart
+// (1024 B of data plus 16 B of padding against bank conflicts).
+// Staging moves 16-byte chunks: an operand whose rows are contiguous in k
+// (A not transposed, B transposed) is copied chunk for chunk; an operand
+// contiguous along M / N is read as 8 x 8 blocks (8 chunks along k) and
+// transposed in registers (byte permutes) on the way.  Ragged or unaligned
+// chunks fall back to element loads with zero fill.  Two slab buffers: the
+// global loads of slab s + 1 are issued while the MMAs of slab s run; one
+// thread issues four tcgen05.mma (M 128, N BN, K 16, BF16 -> FP32 in TMEM)
+// per slab and commits them to that buffer's mbarrier, which frees the buffer
+// again.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
+// TMEM lanes / output rows 32 w .. 32 w + 31) and stores 16-byte vectors where
+// the output is aligned.  Every wait is bounded: on timeout the CTA raises the
+// error flag, skips its tile, drains its MMAs, frees its TMEM and returns.
 // ---------------------------------------------------------------------------
-constexpr int TC_M = 128, TC_N = 64, TC_K = 64;
+constexpr int TC_M = 128, TC_K = 64;
+// Core matrices: k groups 128 B apart (LBO), 8-row groups kTcSbo apart (SBO,
+// padded by 16 B so that stores of different row groups fall on different
+// shared-memory banks).
+constexpr int kTcLbo = 128, kTcSbo = 1040;
 constexpr long long kTcSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ unsigned g_tc_error = 0;
@@ -172,8 +186,8 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
 
 // Instruction descriptor, kind::f16: D F32 (bit 4), A BF16 (bit 7), B BF16
 // (bit 10), both K-major, N >> 3 at [17,23), M >> 4 at [24,29).
-__host__ __device__ constexpr uint32_t tc_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(TC_M >> 4) << 24);
 }
 
@@ -190,93 +204,185 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
-__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
-  __shared__ __align__(1024) uint8_t sA[TC_M * TC_K * 2];
-  __shared__ __align__(1024) uint8_t sB[TC_N * TC_K * 2];
-  __shared__ __align__(8) uint64_t mbar;
+// One operand of the tile: `rows` rows (M or N) of one K slab.
+struct TcOperand {
+  const __nv_bfloat16* p;   // batch base
+  long long ld;             // leading dimension (elements)
+  int row0, nrows;          // first row of the tile, rows of the whole operand
+  int K;
+  bool kcontig;             // element (row, k) at p[row * ld + k] (else p[k * ld + row])
+  bool vec;                 // 16-byte chunks allowed (aligned base, ld, batch stride)
+};
+
+__device__ __forceinline__ __nv_bfloat16 tc_elem(const TcOperand& o, int r, int k) {
+  const int gr = o.row0 + r;
+  if (gr >= o.nrows || k >= o.K) return __float2bfloat16(0.0f);
+  return o.kcontig ? o.p[(long long)gr * o.ld + k] : o.p[(long long)k * o.ld + gr];
+}
+
+// Register copy of this thread's share of one slab of one operand: R rows.
+// K-contiguous: chunk i (i = tid + 128 q) = row i % R, k group i / R.
+// MN-contiguous: block i = (row group i % (R / 8), k group i / (R / 8)), 8 chunks.
+template <int R>
+struct TcStage {
+  static constexpr int kChunks = R * 8 / 128;          // K-contiguous chunks per thread
+  static constexpr int kBlocks = (R / 8) * 8;          // MN-contiguous 8x8 blocks per slab
+  uint4 v[8];
+
+  __device__ __forceinline__ void load(const TcOperand& o, int k0) {
+    const int tid = threadIdx.x;
+    if (o.kcontig) {
+#pragma unroll
+      for (int q = 0; q < kChunks; ++q) {
+        const int i = tid + 128 * q, r = i % R, kg = i / R;
+        const int gr = o.row0 + r, gk = k0 + 8 * kg;
+        if (o.vec && gr < o.nrows && gk + 8 <= o.K) {
+          v[q] = __ldg(reinterpret_cast<const uint4*>(o.p + (long long)gr * o.ld + gk));
+        } else {
+          __nv_bfloat16 e[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) e[j] = tc_elem(o, r, gk + j);
+          memcpy(&v[q], e, 16);
+        }
+      }
+    } else if (tid < kBlocks) {
+      const int rg = tid % (R / 8), kg = tid / (R / 8);
+      const int gr = o.row0 + 8 * rg;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int gk = k0 + 8 * kg + kk;
+        if (o.vec && gr + 8 <= o.nrows && gk < o.K) {
+          v[kk] = __ldg(reinterpret_cast<const uint4*>(o.p + (long long)gk * o.ld + gr));
+        } else {
+          __nv_bfloat16 e[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) e[j] = tc_elem(o, 8 * rg + j, gk);
+          memcpy(&v[kk], e, 16);
+        }
+      }
+    }
+  }
+
+  // Writes the registers into the K-major slab at shared address `base`.
+  __device__ __forceinline__ void store(const TcOperand& o, uint32_t base) {
+    const int tid = threadIdx.x;
+    if (o.kcontig) {
+#pragma unroll
+      for (int q = 0; q < kChunks; ++q) {
+        const int i = tid + 128 * q, r = i % R, kg = i / R;
+        const uint32_t a = base + (uint32_t)((r >> 3) * kTcSbo + kg * kTcLbo + (r & 7) * 16);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n"
+                     :: "r"(a), "r"(v[q].x), "r"(v[q].y), "r"(v[q].z), "r"(v[q].w) : "memory");
+      }
+    } else if (tid < kBlocks) {
+      const int rg = tid % (R / 8), kg = tid / (R / 8);
+      const uint32_t cm = base + (uint32_t)(rg * kTcSbo + kg * kTcLbo);
+      // transpose: output row c (one M / N index) holds k = 0..7; word w of it
+      // pairs k = 2w, 2w + 1, taken from word c / 2 of input chunks 2w, 2w + 1
+      const uint32_t* in = reinterpret_cast<const uint32_t*>(v);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint32_t sel = (c & 1) ? 0x7632u : 0x5410u;
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t lo = in[(2 * q) * 4 + (c >> 1)], hi = in[(2 * q + 1) * 4 + (c >> 1)];
+          w[q] = __byte_perm(lo, hi, sel);
+        }
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n"
+                     :: "r"(cm + c * 16), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
+      }
+    }
+  }
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int vecA, int vecB) {
+  extern __shared__ __align__(1024) uint8_t tc_smem[];
+  constexpr int A_BYTES = (TC_M / 8) * kTcSbo, B_BYTES = (BN / 8) * kTcSbo;
+  constexpr int STAGE = A_BYTES + B_BYTES;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_tile;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * BN;
   const long long b = blockIdx.z;
-  const __nv_bfloat16* A = g.A + b * g.strideA;
-  const __nv_bfloat16* B = g.B + b * g.strideB;
-  const uint32_t bar = smem_u32(&mbar);
+  TcOperand A{g.A + b * g.strideA, g.lda, m0, g.M, g.K, g.transA == 0, vecA != 0};
+  TcOperand B{g.B + b * g.strideB, g.ldb, n0, g.N, g.K, g.transB != 0, vecB != 0};
+  const uint32_t smem0 = smem_u32(tc_smem);
+  const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                 :: "r"(smem_u32(&tmem_slot)), "r"(TC_N) : "memory");
+                 :: "r"(smem_u32(&tmem_slot)), "r"(BN) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(bar1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    abort_tile = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(sA);
-  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(sB);
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+
+  TcStage<TC_M> ra;
+  TcStage<BN> rb;
   const int nslab = (g.K + TC_K - 1) / TC_K;
-  int issued = 0;   // slabs whose MMAs were committed (same value in every thread)
+  int issued = 0;        // slabs whose MMAs were committed (same in every thread)
+  bool abort_tile = false;
+  ra.load(A, 0);
+  rb.load(B, 0);
   for (int sl = 0; sl < nslab; ++sl) {
-    if (sl > 0) {
-      // the MMAs of the previous slab must have read shared memory
-      if (!mbar_wait(bar, (sl - 1) & 1)) abort_tile = 1;
-      __syncthreads();
-      if (abort_tile) break;
-    }
-    const int k0 = sl * TC_K;
-    // element (row, k) of a slab -> core matrix (row / 8, k / 8), 8 core matrices per row group
-    for (int i = tid; i < TC_M * TC_K; i += 128) {
-      int m, k;
-      if (!g.transA) { m = i / TC_K; k = i % TC_K; } else { k = i / TC_M; m = i % TC_M; }
-      const int gm = m0 + m, gk = k0 + k;
-      __nv_bfloat16 v = zero;
-      if (gm < g.M && gk < g.K) v = g.transA ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
-      As[((m >> 3) * 8 + (k >> 3)) * 64 + (m & 7) * 8 + (k & 7)] = v;
-    }
-    for (int i = tid; i < TC_N * TC_K; i += 128) {
-      int n, k;
-      if (!g.transB) { k = i / TC_N; n = i % TC_N; } else { n = i / TC_K; k = i % TC_K; }
-      const int gn = n0 + n, gk = k0 + k;
-      __nv_bfloat16 v = zero;
-      if (gn < g.N && gk < g.K) v = g.transB ? B[(long long)gn * g.ldb + gk] : B[(long long)gk * g.ldb + gn];
-      Bs[((n >> 3) * 8 + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = v;
+    const int buf = sl & 1;
+    const uint32_t sa = smem0 + buf * STAGE, sb = sa + A_BYTES;
+    bool ok = true;
+    // buffer `buf` was last read by the MMAs of slab sl - 2
+    if (sl >= 2) ok = mbar_wait(buf ? bar1 : bar0, ((sl - 2) >> 1) & 1);
+    if (ok) {
+      ra.store(A, sa);
+      rb.store(B, sb);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
+    if (__syncthreads_or(!ok)) { abort_tile = true; break; }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int kk = 0; kk < TC_K / 16; ++kk) {
-        const uint64_t da = tc_desc(a_base + kk * 256, 128, 1024);
-        const uint64_t db = tc_desc(b_base + kk * 256, 128, 1024);
+        const uint64_t da = tc_desc(sa + kk * 2 * kTcLbo, kTcLbo, kTcSbo);
+        const uint64_t db = tc_desc(sb + kk * 2 * kTcLbo, kTcLbo, kTcSbo);
         const uint32_t acc = (sl > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-            :: "r"(tmem), "l"(da), "l"(db), "r"(tc_idesc()), "r"(acc) : "memory");
+            :: "r"(tmem), "l"(da), "l"(db), "r"(tc_idesc(BN)), "r"(acc) : "memory");
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                   :: "r"(bar) : "memory");
+                   :: "r"(buf ? bar1 : bar0) : "memory");
     }
     issued = sl + 1;
+    // the next slab's global loads overlap these MMAs
+    if (sl + 1 < nslab) {
+      ra.load(A, (sl + 1) * TC_K);
+      rb.load(B, (sl + 1) * TC_K);
+    }
   }
   if (!abort_tile) {
-    if (!mbar_wait(bar, (nslab - 1) & 1)) abort_tile = 1;
+    const int last = nslab - 1;
+    const bool ok = mbar_wait((last & 1) ? bar1 : bar0, (last >> 1) & 1);
+    abort_tile = __syncthreads_or(!ok);
   }
-  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (!abort_tile) {
     float* C = g.C ? g.C + b * g.strideC : nullptr;
     __nv_bfloat16* D = g.D ? g.D + b * g.strideC : nullptr;
     const int row = m0 + warp * 32 + lane;
+    // 16-byte stores need 4 (f32) / 8 (bf16) aligned columns, row pitch and base
+    const bool vc = C && (g.ldc % 4 == 0) && (g.strideC % 4 == 0) &&
+                    ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
+    const bool vd = D && (g.ldc % 8 == 0) && (g.strideC % 8 == 0) &&
+                    ((reinterpret_cast<uintptr_t>(g.D) & 15) == 0);
 #pragma unroll
-    for (int c0 = 0; c0 < TC_N; c0 += 8) {
+    for (int c0 = 0; c0 < BN; c0 += 8) {
       uint32_t r[8];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
       asm volatile(
@@ -285,35 +391,72 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
             "=r"(r[7])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (row < g.M) {
+      const int col0 = n0 + c0;
+      if (row >= g.M || col0 >= g.N) continue;
+      const long long o = (long long)row * g.ldc + col0;
+      float v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int col = n0 + c0 + e;
-          if (col >= g.N) continue;
-          const long long o = (long long)row * g.ldc + col;
-          float v = g.alpha * __uint_as_float(r[e]);
-          if (g.epilogue == RLBM_EPI_ATOMIC) {
-            atomicAdd(C + o, v);
-            continue;
-          }
-          if (C && g.beta != 0.f) v += g.beta * C[o];
-          if (g.bias) v += g.bias[col];
-          if (C) C[o] = v;
-          if (D) D[o] = __float2bfloat16_rn(g.epilogue == RLBM_EPI_GELU ? gelu(v) : v);
+      for (int e = 0; e < 8; ++e) v[e] = g.alpha * __uint_as_float(r[e]);
+      const bool full = col0 + 8 <= g.N;
+      if (g.epilogue == RLBM_EPI_ATOMIC) {
+        if (vc && full) {
+          atomicAdd(reinterpret_cast<float4*>(C + o), make_float4(v[0], v[1], v[2], v[3]));
+          atomicAdd(reinterpret_cast<float4*>(C + o + 4), make_float4(v[4], v[5], v[6], v[7]));
+        } else {
+          for (int e = 0; e < 8 && col0 + e < g.N; ++e) atomicAdd(C + o + e, v[e]);
+        }
+        continue;
+      }
+      if (C && g.beta != 0.f) {
+        if (vc && full) {
+          const float4 p = *reinterpret_cast<const float4*>(C + o);
+          const float4 q = *reinterpret_cast<const float4*>(C + o + 4);
+          v[0] += g.beta * p.x; v[1] += g.beta * p.y; v[2] += g.beta * p.z; v[3] += g.beta * p.w;
+          v[4] += g.beta * q.x; v[5] += g.beta * q.y; v[6] += g.beta * q.z; v[7] += g.beta * q.w;
+        } else {
+          for (int e = 0; e < 8 && col0 + e < g.N; ++e) v[e] += g.beta * C[o + e];
+        }
+      }
+      if (g.bias) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) if (col0 + e < g.N) v[e] += g.bias[col0 + e];
+      }
+      if (C) {
+        if (vc && full) {
+          *reinterpret_cast<float4*>(C + o) = make_float4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<float4*>(C + o + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+          for (int e = 0; e < 8 && col0 + e < g.N; ++e) C[o + e] = v[e];
+        }
+      }
+      if (D) {
+        __nv_bfloat16 h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          h[e] = __float2bfloat16_rn(g.epilogue == RLBM_EPI_GELU ? gelu(v[e]) : v[e]);
+        if (vd && full) {
+          uint4 u;
+          memcpy(&u, h, 16);
+          *reinterpret_cast<uint4*>(D + o) = u;
+        } else {
+          for (int e = 0; e < 8 && col0 + e < g.N; ++e) D[o + e] = h[e];
         }
       }
     }
   } else {
     if (tid == 0) atomicOr(&g_tc_error, 1u);
     // let the last committed MMAs finish (bounded) before the TMEM is freed
-    if (issued > 0) mbar_wait(bar, (issued - 1) & 1);
+    if (issued > 0) mbar_wait(((issued - 1) & 1) ? bar1 : bar0, ((issued - 1) >> 1) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(TC_N)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(BN)
                  : "memory");
 }
+
+template <int BN>
+constexpr int tc_smem_bytes() { return 2 * ((TC_M / 8) * kTcSbo + (BN / 8) * kTcSbo); }
 
 // ---------------------------------------------------------------------------
 // Spectral mixing.  S, U: [batch][KX][2][KY][C]; R: [KX][KY][C][C][2].
@@ -453,14 +596,38 @@ __global__ void k_mse_grad(const float* __restrict__ Y, const float* __restrict_
   dY[i] = 2.0f * m[r] * (Y[i] - T[i]) * inv;
 }
 
-__global__ void k_colsum(const float* __restrict__ X, float* out, long long rows, int cols) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= cols) return;
-  const long long chunk = (rows + gridDim.y - 1) / gridDim.y;
-  const long long r0 = blockIdx.y * chunk, r1 = r0 + chunk < rows ? r0 + chunk : rows;
-  float s = 0.f;
-  for (long long r = r0; r < r1; ++r) s += X[r * cols + j];
-  atomicAdd(out + j, s);
+// Column sums of X [rows][cols] added to out.  With cols <= 256, a block of
+// 256 threads covers 256 / cols rows per pass (thread t: column t % cols, row
+// t / cols; coalesced), walks the rows with a grid stride, and reduces the
+// per-thread partial sums of each column in shared memory before one atomic
+// add per column.  Wider matrices: one column per thread, looped.
+constexpr int kColsumThreads = 256;
+
+__global__ void __launch_bounds__(kColsumThreads) k_colsum(const float* __restrict__ X, float* out,
+                                                           long long rows, int cols) {
+  __shared__ float part[kColsumThreads];
+  const int t = threadIdx.x;
+  if (cols <= kColsumThreads) {
+    const int rpp = kColsumThreads / cols;             // rows per pass
+    const int j = t % cols, rr = t / cols;
+    float s = 0.f;
+    if (rr < rpp)
+      for (long long r = (long long)blockIdx.x * rpp + rr; r < rows; r += (long long)gridDim.x * rpp)
+        s += X[r * cols + j];
+    part[t] = rr < rpp ? s : 0.f;
+    __syncthreads();
+    if (t < cols) {
+      float c = 0.f;
+      for (int k = 0; k < rpp; ++k) c += part[k * cols + t];
+      atomicAdd(out + t, c);
+    }
+  } else {
+    for (int j = t; j < cols; j += kColsumThreads) {
+      float s = 0.f;
+      for (long long r = blockIdx.x; r < rows; r += gridDim.x) s += X[r * cols + j];
+      atomicAdd(out + j, s);
+    }
+  }
 }
 
 __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
@@ -545,9 +712,33 @@ int rlbm_gemm_bf16_tc(int transA, int transB, int M, int N, int K, float alpha, 
   g.B = static_cast<const __nv_bfloat16*>(B); g.ldb = ldb; g.strideB = strideB;
   g.C = C; g.ldc = ldc; g.strideC = strideC;
   g.bias = bias; g.D = static_cast<__nv_bfloat16*>(D); g.epilogue = epilogue;
-  dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M, batch);
-  if (grid.y > 65535) return RLBM_EINVAL;
-  k_gemm_tc<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(g);
+  // 16-byte operand chunks need aligned bases, leading dimensions and strides
+  const bool vecA = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && lda % 8 == 0 &&
+                    strideA % 8 == 0;
+  const bool vecB = ((reinterpret_cast<uintptr_t>(B) & 15) == 0) && ldb % 8 == 0 &&
+                    strideB % 8 == 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned gy = (unsigned)((M + TC_M - 1) / TC_M);
+  if (gy > 65535) return RLBM_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RLBM_ECUDA;
+  static bool smem_set[64][3] = {};
+  auto launch = [&](auto kernel, int bn, int slot, int bytes) -> int {
+    if (!smem_set[dev][slot]) {
+      if (cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               bytes) != cudaSuccess)
+        return RLBM_ECUDA;
+      smem_set[dev][slot] = true;
+    }
+    dim3 grid((unsigned)((N + bn - 1) / bn), gy, (unsigned)batch);
+    kernel<<<grid, 128, bytes, st>>>(g, (int)vecA, (int)vecB);
+    return RLBM_OK;
+  };
+  int r;
+  if (N <= 32) r = launch(k_gemm_tc<32>, 32, 0, tc_smem_bytes<32>());
+  else if (N <= 64) r = launch(k_gemm_tc<64>, 64, 1, tc_smem_bytes<64>());
+  else r = launch(k_gemm_tc<128>, 128, 2, tc_smem_bytes<128>());
+  if (r != RLBM_OK) return r;
   return status();
 }
 
@@ -610,8 +801,9 @@ int rlbm_fno_mse(const float* Y, const float* target, const float* mask, float* 
 
 int rlbm_fno_colsum(const float* X, float* out, long long rows, int cols, void* stream) {
   if (rows <= 0 || cols <= 0) return RLBM_EINVAL;
-  dim3 grid((cols + 127) / 128, (unsigned)(rows < 512 ? rows : 512));
-  k_colsum<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(X, out, rows, cols);
+  const long long passes = cols <= kColsumThreads ? rows / (kColsumThreads / cols) + 1 : rows;
+  const int grid = (int)(passes < 1216 ? passes : 1216);
+  k_colsum<<<grid, kColsumThreads, 0, static_cast<cudaStream_t>(stream)>>>(X, out, rows, cols);
   return status();
 }
 

@@ -30,8 +30,8 @@ import numpy as np
 from . import rlbm
 
 EPI_NONE, EPI_GELU, EPI_ATOMIC = 0, 1, 2
-# GEMM back ends: "mma" = warp-level mma.sync m16n8k16, "tc" = tcgen05 with
-# the accumulator in tensor memory
+# GEMM back ends: "tc" (default) = tcgen05 with the accumulator in tensor
+# memory, "mma" = warp-level mma.sync m16n8k16 (kept as a cross-check)
 GEMM_IMPLS = {"mma": "rlbm_gemm_bf16", "tc": "rlbm_gemm_bf16_tc"}
 
 _FNO_EXPORTS = {
@@ -116,7 +116,7 @@ class FNO:
     BF16 shadow used by the GEMMs."""
 
     def __init__(self, cfg: FNOConfig, batch: int, seed: int = 0, device="cuda",
-                 gemm_impl: str = "mma"):
+                 gemm_impl: str = "tc"):
         import torch
         self.torch = torch
         self.cfg, self.B = cfg, batch
@@ -223,14 +223,19 @@ class FNO:
         _ok(rc, "gemm")
 
     def gemm_tn_sum(self, A16, B16, M, N, K, out):
-        """out (f32 [M, N]) += A^T B with A [K, M], B [K, N] bf16 (split over K)."""
-        chunk = 4096
-        nb = (K + chunk - 1) // chunk
-        if K % chunk:
-            chunk = K  # ragged: one chunk
-            nb = 1
-        self.gemm(A16, B16, M, N, chunk, lda=M, ldb=N, transA=1, C=out, ldc=N, epi=EPI_ATOMIC,
-                  batch=nb, sA=chunk * M, sB=chunk * N, sC=0)
+        """out (f32 [M, N]) += A^T B with A [K, M], B [K, N] bf16: split-K over
+        chunks of 512 rows (one block each, atomic accumulation into out); a
+        ragged remainder is a second call."""
+        chunk = 512
+        nb = K // chunk
+        if nb:
+            self.gemm(A16, B16, M, N, chunk, lda=M, ldb=N, transA=1, C=out, ldc=N,
+                      epi=EPI_ATOMIC, batch=nb, sA=chunk * M, sB=chunk * N, sC=0)
+        rem = K - nb * chunk
+        if rem:
+            A = A16.reshape(K, M)[nb * chunk:]
+            B = B16.reshape(K, N)[nb * chunk:]
+            self.gemm(A, B, M, N, rem, lda=M, ldb=N, transA=1, C=out, ldc=N, epi=EPI_ATOMIC)
 
     def to16(self, x, y):
         _ok(self.lib.rlbm_fno_to_bf16(_p(x), _p(y), x.numel(), self._stream()), "to_bf16")

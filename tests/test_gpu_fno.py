@@ -159,3 +159,38 @@ def test_adam_step_reduces_loss(env):
         net.backward()
         net.adam(lr=3e-3)
     assert losses[-1] < 0.7 * losses[0]
+
+
+@pytest.mark.parametrize("rows,cols", [(1, 1), (1000, 4), (5000, 32), (777, 128), (300, 300)])
+def test_colsum_matches_numpy(env, rows, cols):
+    torch, fno = env
+    import ctypes
+    rng = np.random.default_rng(rows + cols)
+    X = rng.standard_normal((rows, cols)).astype(np.float32)
+    out0 = rng.standard_normal(cols).astype(np.float32)
+    Xt = torch.tensor(X, device="cuda")
+    ot = torch.tensor(out0, device="cuda")
+    assert fno._lib().rlbm_fno_colsum(ctypes.c_void_p(Xt.data_ptr()), ctypes.c_void_p(ot.data_ptr()),
+                                      rows, cols, None) == 0
+    torch.cuda.synchronize()
+    ref = out0.astype(np.float64) + X.astype(np.float64).sum(0)
+    assert np.abs(ot.cpu().numpy() - ref).max() <= 1e-5 * (1 + np.abs(X).sum(0).max())
+
+
+@pytest.mark.parametrize("impl", ["mma", "tc"])
+def test_split_k_weight_gradient_with_ragged_rows(env, impl):
+    """out += A^T B over K rows, split into 512-row chunks plus a remainder."""
+    torch, fno = env
+    net = fno.FNO(fno.FNOConfig(N=8, C=8, Cq=8, L=1, m1=2, m2=2), batch=1, gemm_impl=impl)
+    rng = np.random.default_rng(9)
+    K, M, N = 1300, 24, 40
+    A = bf16_round(rng.standard_normal((K, M)))
+    B = bf16_round(rng.standard_normal((K, N)))
+    out0 = rng.standard_normal((M, N))
+    At = torch.tensor(A, dtype=torch.bfloat16, device="cuda")
+    Bt = torch.tensor(B, dtype=torch.bfloat16, device="cuda")
+    ot = torch.tensor(out0, dtype=torch.float32, device="cuda")
+    net.gemm_tn_sum(At, Bt, M, N, K, ot)
+    torch.cuda.synchronize()
+    ref = out0 + A.T @ B
+    assert np.abs(ot.cpu().numpy() - ref).max() <= 1e-5 * (np.abs(A).T @ np.abs(B)).max() + 1e-5
