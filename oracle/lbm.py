@@ -47,6 +47,15 @@ Readings of points the paper leaves open (each also listed in the design notes):
     initial fields; step 1 starts with streaming.
   * Macroscopic fields at time t are the moments of the streamed populations
     at t (the values the next collision uses).
+  * Electric force, local capacitance approximation (Sec. 3, Eq. lca):
+    phi = -e n / C_g.  Reading: the force pushes electrons away from high
+    density (like charges repel), F_E = -(e^2 / C_g) grad n per particle; the
+    printed E = -rho_e grad phi, taken literally with e > 0, would point the
+    other way.  e = 1, and inv_cg = e^2 / C_g.  The gradient is taken in the
+    length unit of c = 1 (one hop of 5 sites), with central differences of
+    the density of the previous time step (one-sided at walled edges, wrapped
+    on periodic axes); at the first step the initial density field.  F_E adds
+    to the uniform force F of the sample.
 """
 from __future__ import annotations
 
@@ -183,8 +192,10 @@ def forcing(n, ux, uy, T, Fx, Fy):
     return t.w.reshape((-1,) + ex) * (n / T) * (Fv * (Q - dQ0) - (Fx * dQx + Fy * dQy))
 
 
-def collide(delta, tau, Fx=0.0, Fy=0.0):
-    """Relaxation + forcing of Eq. discrete-rbe on streamed deviations [48, ...]."""
+def collide(delta, tau, Fx=0.0, Fy=0.0, return_dn=False):
+    """Relaxation + forcing of Eq. discrete-rbe on streamed deviations [48, ...].
+    Fx, Fy: force per particle, scalars or per-site arrays.  With return_dn,
+    also returns n - 1 of the streamed populations."""
     t = tables()
     dN, dT = moments(delta)
     dn, ux, uy, dTT, _ = landau_dev(dN, dT)
@@ -197,9 +208,9 @@ def collide(delta, tau, Fx=0.0, Fy=0.0):
                   - t.P[2].reshape((-1,) + ex) * uy)
     omega = pU / (t.P[0].reshape((-1,) + ex) * tau)
     out = delta - omega * (delta - deq)
-    if Fx != 0.0 or Fy != 0.0:
+    if np.any(np.asarray(Fx) != 0.0) or np.any(np.asarray(Fy) != 0.0):
         out = out + forcing(n, ux, uy, T, Fx, Fy)
-    return out
+    return (out, dn) if return_dn else out
 
 
 # ---------------------------------------------------------------------------
@@ -218,6 +229,7 @@ class Lattice:
         self.px, self.py = bool(sample.periodic_x), bool(sample.periodic_y)
         self.tau = float(sample.tau)
         self.Fx, self.Fy = float(sample.Fx), float(sample.Fy)
+        self.inv_cg = float(getattr(sample, "inv_cg", 0.0))   # e^2 / C_g; 0: no electric force
         self.contacts = list(sample.contacts)
         for c in self.contacts:
             if c.edge in (0, 1) and self.py or c.edge in (2, 3) and self.px:
@@ -265,6 +277,28 @@ class Lattice:
         self.ghost = np.array([self.contact_deviation(c) for c in self.contacts]) \
             if self.contacts else np.zeros((0, quadrature.Q))
 
+    def grad(self, a):
+        """(d/dx, d/dy) of a site field [ny, nx] in the length unit of c = 1
+        (5 sites): central differences, one-sided at walled edges, wrapped on
+        periodic axes."""
+        def d(axis, periodic):
+            m = a.shape[axis]
+            if periodic:
+                g = (np.roll(a, -1, axis) - np.roll(a, 1, axis)) / 2.0
+            else:
+                g = np.empty_like(a)
+                sl = lambda i: tuple(slice(None) if k != axis else i for k in range(2))
+                g[sl(slice(1, m - 1))] = (a[sl(slice(2, m))] - a[sl(slice(0, m - 2))]) / 2.0
+                g[sl(0)] = a[sl(1)] - a[sl(0)]
+                g[sl(m - 1)] = a[sl(m - 1)] - a[sl(m - 2)]
+            return 5.0 * g
+        return d(1, self.px), d(0, self.py)
+
+    def electric_force(self, dn_prev):
+        """F_E = -(e^2 / C_g) grad n per particle from the previous step's n - 1."""
+        gx, gy = self.grad(dn_prev)
+        return -self.inv_cg * gx, -self.inv_cg * gy
+
     def stream(self, post):
         """Pull-streaming with periodic wrap, contacts and bounce-back walls."""
         t = tables()
@@ -291,6 +325,8 @@ def init(lat: Lattice, n, ux, uy, T):
 
 def step(lat: Lattice, post):
     """One time step: stream then collide.  Returns the new post-collision state."""
+    if lat.inv_cg != 0.0:
+        raise ValueError("a sample with an electric force steps with step_lca")
     return collide(lat.stream(post), lat.tau, lat.Fx, lat.Fy)
 
 
@@ -298,6 +334,20 @@ def run(lat: Lattice, post, nsteps):
     for _ in range(nsteps):
         post = step(lat, post)
     return post
+
+
+def step_lca(lat: Lattice, post, dn_prev):
+    """One time step with the electric force of the local capacitance
+    approximation: F = (Fx, Fy) + F_E(grad of the previous step's density).
+    Returns (post-collision state, n - 1 of this step)."""
+    ex, ey = lat.electric_force(dn_prev)
+    return collide(lat.stream(post), lat.tau, lat.Fx + ex, lat.Fy + ey, return_dn=True)
+
+
+def run_lca(lat: Lattice, post, dn_prev, nsteps):
+    for _ in range(nsteps):
+        post, dn_prev = step_lca(lat, post, dn_prev)
+    return post, dn_prev
 
 
 def macroscopic(lat: Lattice, post):
