@@ -83,7 +83,17 @@ typedef struct {
 } rlbm_contact;
 
 /* One sample: an nx x ny rectangle, periodic or walled per axis, relaxation
- * time tau (> 0.5), uniform body force (Fx, Fy) per particle, contacts. */
+ * time tau (> 0.5), uniform body force (Fx, Fy) per particle, contacts, and
+ * the electric force of the local capacitance approximation (Sec. 3, Eq. lca:
+ * phi = -e n / C_g): inv_cg = e^2 / C_g in lattice units (e = 1), 0 for none
+ * (C_g infinite).  With inv_cg > 0 every site adds
+ *     F_E = -inv_cg grad n
+ * to (Fx, Fy), the gradient taken from the previous time step's density over
+ * one hop (5 sites, the length unit of c = 1): (n(x+5) - n(x-5)) / 2, forward
+ * or backward over 5 sites next to a walled edge, wrapped on periodic axes;
+ * the first step uses the density given to rlbm_init.  0 <= inv_cg < 1e3;
+ * the explicit force is stable up to about inv_cg = 0.3 at tau = 0.8
+ * (measured; the paper's C_g = 10 is 0.1). */
 typedef struct {
   int nx, ny;
   int periodic_x, periodic_y;
@@ -91,6 +101,7 @@ typedef struct {
   double Fx, Fy;
   int ncontacts;
   rlbm_contact contacts[RLBM_MAX_CONTACTS];
+  double inv_cg;
 } rlbm_sample;
 
 typedef struct {
@@ -169,7 +180,10 @@ int rlbm_moments(rlbm_ctx* ctx, int sample, double* n, double* ux, double* uy,
                  double* T, int device_ptrs);
 
 /* Stored post-collision state of `sample` as deviations f_i - w_i, layout
- * [48][ny][nx] FP64 (checkpoint / restart and one-step checks). */
+ * [48][ny][nx] FP64 (checkpoint / restart and one-step checks).  With the
+ * electric force on, rlbm_set_state also sets the density the next step's
+ * force uses, to the density of the restored state (the previous step's
+ * density is not part of the checkpoint). */
 int rlbm_get_state(rlbm_ctx* ctx, int sample, double* delta, int device_ptrs);
 int rlbm_set_state(rlbm_ctx* ctx, int sample, const double* delta, int device_ptrs);
 

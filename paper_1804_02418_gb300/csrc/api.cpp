@@ -32,6 +32,8 @@ struct SampleLayout {
   DevSample dev;
   size_t buf_off[2];     // byte offsets of the two population buffers
   size_t buf_bytes;
+  size_t dn_off[2];      // byte offsets of the two density planes (electric force only)
+  size_t dn_bytes;       // 0 without the electric force
   long long sites;
   double ghost[kMaxContacts][kQ];   // contact deviations f^eq - w
 };
@@ -76,6 +78,7 @@ std::string check_sample(const rlbm_sample& s) {
   if ((long long)s.nx * s.ny > (1LL << 31)) return "sample has more than 2^31 sites";
   if (!(s.tau > 0.5) || !std::isfinite(s.tau)) return "tau must be > 0.5";
   if (!(std::fabs(s.Fx) < 1e-2) || !(std::fabs(s.Fy) < 1e-2)) return "|F| must be < 1e-2";
+  if (!(s.inv_cg >= 0.0) || !(s.inv_cg < 1e3)) return "inv_cg must be in [0, 1e3)";
   if (s.ncontacts < 0 || s.ncontacts > RLBM_MAX_CONTACTS) return "ncontacts out of range";
   for (int k = 0; k < s.ncontacts; ++k) {
     const rlbm_contact& c = s.contacts[k];
@@ -126,7 +129,7 @@ struct rlbm_ctx {
   cudaGraphExec_t graph[2];   // graph_steps steps starting from buffer 0 / 1
   size_t dsamples_off, tiles_off[3];
   long long ntiles[3];
-  bool force_any;
+  int force_any;             // kForce* level the batched launch needs (highest of the samples)
   int sm_count;
   std::vector<double> sample_res;
 };
@@ -171,6 +174,12 @@ size_t plan(const rlbm_config* cfg, const PrecOps* ops, rlbm_ctx* out) {
     l.buf_off[0] = off;
     l.buf_off[1] = off + l.buf_bytes;
     off += 2 * l.buf_bytes;
+    if (s.inv_cg != 0.0) {
+      l.dn_bytes = align_up((size_t)plane * ops->real_bytes, 256);
+      l.dn_off[0] = off;
+      l.dn_off[1] = off + l.dn_bytes;
+      off += 2 * l.dn_bytes;
+    }
     l.sites = (long long)s.nx * s.ny;
     DevSample& d = l.dev;
     d.nx = s.nx; d.ny = s.ny; d.ldx = ldx;
@@ -183,6 +192,9 @@ size_t plan(const rlbm_config* cfg, const PrecOps* ops, rlbm_ctx* out) {
     d.off[1] = (long long)(l.buf_off[1] / ops->elem_bytes);
     d.inv_tau = 1.0 / s.tau;
     d.Fx = s.Fx; d.Fy = s.Fy;
+    d.inv_cg = s.inv_cg;
+    d.dn[0] = d.dn[1] = nullptr;     // bound to the workspace by rlbm_create
+    d.cur = 0;
     for (int k = 0; k < s.ncontacts; ++k) {
       d.cedge[k] = s.contacts[k].edge;
       d.clo[k] = s.contacts[k].x0;
@@ -349,8 +361,11 @@ cudaError_t launch_step(rlbm_ctx* c, int from, int res, int bx, int grid, int st
   if (bx == 0) {
     for (size_t i = 0; i < c->samples.size(); ++i) {
       SampleLayout& L = c->samples[i];
-      const bool force = L.desc.Fx != 0.0 || L.desc.Fy != 0.0;
-      cudaError_t e = c->ops->step(buf(c, (int)i, from), buf(c, (int)i, from ^ 1), L.dev,
+      const int force = L.desc.inv_cg != 0.0 ? kForceLca
+                      : (L.desc.Fx != 0.0 || L.desc.Fy != 0.0) ? kForceUniform : kForceNone;
+      DevSample d = L.dev;
+      d.cur = from;
+      cudaError_t e = c->ops->step(buf(c, (int)i, from), buf(c, (int)i, from ^ 1), d,
                                    ghost_ptr(c, (int)i), force, res, uprev, acc + 2 * i, err,
                                    c->stream);
       if (e != cudaSuccess) return e;
@@ -480,9 +495,13 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out) {
   c->graph_steps = cfg->graph_steps > 0 ? cfg->graph_steps : 0;
   if (c->graph_steps & 1) c->graph_steps += 1;          // even: a replay keeps the buffer parity
   c->tune_cache = cfg->tune_cache ? cfg->tune_cache : "";
-  c->force_any = false;
-  for (int i = 0; i < cfg->nsamples; ++i)
-    c->force_any |= cfg->samples[i].Fx != 0.0 || cfg->samples[i].Fy != 0.0;
+  c->force_any = kForceNone;
+  for (int i = 0; i < cfg->nsamples; ++i) {
+    const rlbm_sample& si = cfg->samples[i];
+    const int f = si.inv_cg != 0.0 ? kForceLca
+                : (si.Fx != 0.0 || si.Fy != 0.0) ? kForceUniform : kForceNone;
+    c->force_any = std::max(c->force_any, f);
+  }
   cudaGetDevice(&c->device);
   c->sm_count = 0;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
@@ -507,6 +526,9 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out) {
     c->owns_workspace = true;
   }
   c->ws_bytes = need;
+  for (auto& L : c->samples)
+    if (L.dn_bytes)
+      for (int k = 0; k < 2; ++k) L.dev.dn[k] = c->ws + L.dn_off[k];
   c->sample_res.assign(c->samples.size(), 0.0);
   cudaError_t e = cudaMallocHost((void**)&c->host_pinned,
                                  (2 * c->samples.size() + 2) * sizeof(double));
@@ -557,6 +579,8 @@ int rlbm_init(rlbm_ctx* c, int sample, const double* n, const double* ux, const 
   cudaError_t e;
   if (nnull == 4) {
     e = cudaMemsetAsync(dst, 0, L.buf_bytes, c->stream);   // rest state: f = w, delta = 0
+    if (e == cudaSuccess && L.dn_bytes)                     // and n - 1 = 0
+      e = cudaMemsetAsync(c->ws + L.dn_off[c->cur], 0, L.dn_bytes, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
   } else {
     const double* fp[4] = {n, ux, uy, T};
@@ -570,7 +594,9 @@ int rlbm_init(rlbm_ctx* c, int sample, const double* n, const double* ux, const 
       if (e != cudaSuccess) return cuda_fail(c, e, "field upload");
       dp[f] = d;
     }
-    e = c->ops->init(dst, L.dev, dp[0], dp[1], dp[2], dp[3], at<unsigned>(c, c->err_off),
+    DevSample d = L.dev;
+    d.cur = c->cur;      // the electric force's first step reads this density plane
+    e = c->ops->init(dst, d, dp[0], dp[1], dp[2], dp[3], at<unsigned>(c, c->err_off),
                      c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     c->launches++;
@@ -780,7 +806,8 @@ int rlbm_moments(rlbm_ctx* c, int sample, double* n, double* ux, double* uy, dou
   for (int f = 0; f < 4; ++f)
     dp[f] = !outp[f] ? nullptr : device_ptrs ? outp[f] : stage + (size_t)f * L.sites;
   cudaError_t e = c->ops->moments(buf(c, sample, c->cur), L.dev, ghost_ptr(c, sample), dp[0],
-                                  dp[1], dp[2], dp[3], at<unsigned>(c, c->err_off), c->stream);
+                                  dp[1], dp[2], dp[3], at<unsigned>(c, c->err_off), nullptr,
+                                  c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
   c->launches++;
   if (!device_ptrs) {
@@ -843,6 +870,14 @@ int rlbm_set_state(rlbm_ctx* c, int sample, const double* delta, int device_ptrs
       e = cudaStreamSynchronize(c->stream);   // staging is reused by the next chunk
       if (e != cudaSuccess) return cuda_fail(c, e, "sync");
     }
+  }
+  if (L.dn_bytes) {
+    // the electric force of the next step: density of the restored state
+    cudaError_t e = c->ops->moments(buf(c, sample, c->cur), L.dev, ghost_ptr(c, sample), nullptr,
+                                    nullptr, nullptr, nullptr, at<unsigned>(c, c->err_off),
+                                    c->ws + L.dn_off[c->cur], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "density kernel");
+    c->launches++;
   }
   c->sample_ready[sample] = 1;
   c->initialised = std::all_of(c->sample_ready.begin(), c->sample_ready.end(),

@@ -22,6 +22,12 @@ namespace rlbm {
 
 constexpr int kBX = 128;   // threads per block along x; one block row per y
 
+// FORCE template argument of the step kernels: no force, a uniform force per
+// particle, or a uniform force plus the electric force of the local
+// capacitance approximation (its own instantiation, so that the others do not
+// carry its registers).
+constexpr int kForceNone = 0, kForceUniform = 1, kForceLca = 2;
+
 template <typename R>
 struct StepAux {
   R* uprev;              // [sites] x 2 velocity plane for the residual (or null)
@@ -338,6 +344,28 @@ __device__ __forceinline__ void balance(const R* in, const R* out, const C& qc, 
   }
 }
 
+// Gradient of the previous step's n - 1 at (x, y) over one hop (5 sites, the
+// length unit of c = 1): (a(x + 5) - a(x - 5)) / 2 where both exist, the
+// forward or backward difference over 5 sites next to a walled edge, wrapped
+// on periodic axes (Sec. 3, local capacitance approximation; a difference over
+// neighbouring sites would drive density structure finer than a hop).
+template <typename R>
+__device__ __forceinline__ void lca_gradient(const DevSample& s, const R* __restrict__ p, int x,
+                                             int y, R& gx, R& gy) {
+  constexpr int h = kRadius;
+  int xm = x - h, xp = x + h, ym = y - h, yp = y + h;
+  R hx = R(0.5), hy = R(0.5);
+  if (s.periodic_x) { xm = xm < 0 ? xm + s.nx : xm; xp = xp >= s.nx ? xp - s.nx : xp; }
+  else if (xm < 0) { xm = x; hx = R(1); }
+  else if (xp >= s.nx) { xp = x; hx = R(1); }
+  if (s.periodic_y) { ym = ym < 0 ? ym + s.ny : ym; yp = yp >= s.ny ? yp - s.ny : yp; }
+  else if (ym < 0) { ym = y; hy = R(1); }
+  else if (yp >= s.ny) { yp = y; hy = R(1); }
+  const long long row = (long long)y * s.ldx;
+  gx = (p[row + xp] - p[row + xm]) * hx;
+  gy = (p[(long long)yp * s.ldx + x] - p[(long long)ym * s.ldx + x]) * hy;
+}
+
 // Gathers the 48 deviations streamed into site (x < nx, y): from HBM or from
 // the staged slot rows.  All 32 threads of a warp must hold consecutive x of
 // the same row (the interior test is per warp).
@@ -361,13 +389,16 @@ __device__ __forceinline__ void gather(const S* __restrict__ fin, const DevSampl
 // Collision of the gathered deviations f of site (x < nx, y) and store of the
 // 48 new deviations into fout.  RES: 0 nothing extra; 1 store u for the
 // residual; 2 add |u - u_prev|^2 and |u|^2 to r_du2, r_u2 (the caller
-// reduces them).
-template <typename S, bool FORCE, int RES, class C>
+// reduces them).  dn_prev / dn_next: the electric force's density planes of
+// the previous and of this step (used when s.inv_cg != 0).
+template <typename S, int FORCE, int RES, class C>
 __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* __restrict__ fout,
                                               const DevSample& s, int x, int y,
                                               const StepAux<typename Codec<S>::R>& aux,
                                               const C& qc, double& r_du2, double& r_u2,
-                                              uint32_t park) {
+                                              uint32_t park,
+                                              const typename Codec<S>::R* dn_prev,
+                                              typename Codec<S>::R* dn_next) {
   using R = typename Codec<S>::R;
   // FP32 storage: the FP32 quadrature constants satisfy Eq. orthonormal only
   // to ~1e-7, which would break the exact conservation of N^0 and T^0a by the
@@ -377,6 +408,11 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
   // by a correction on the (5,0)-type directions (solved with the constants P**, px).
   constexpr bool kProject = sizeof(S) == sizeof(float);
   {
+    // electric force (local capacitance approximation): the neighbours'
+    // density of the previous step, loaded before the long arithmetic
+    const bool lca = FORCE == kForceLca && s.inv_cg != 0.0;
+    R egx = R(0), egy = R(0);
+    if (lca) lca_gradient(s, dn_prev, x, y, egx, egy);
     const Moments<R> m = moments(f, qc);
     // park: entry of direction d at park + d * blockDim.x * 16
     const uint32_t park_stride = blockDim.x * 16u;
@@ -398,8 +434,10 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
     const R nmT = (M.dn - M.dT) * inv1T;
     const R gt = M.gamma * R(s.inv_tau);
     const R gux = gt * M.ux, guy = gt * M.uy;
-    const R Fx = R(s.Fx), Fy = R(s.Fy);
+    const R Fx = lca ? R(s.Fx) + (-R(s.inv_cg) * egx) : R(s.Fx);
+    const R Fy = lca ? R(s.Fy) + (-R(s.inv_cg) * egy) : R(s.Fy);
     const long long site = (long long)y * s.ldx + x;
+    if (lca) dn_next[site] = M.dn;
     R rN = R(0), rE = R(0), rX = R(0), rY = R(0);
     // (5,0)-type pairs first: in reduced precision they take the correction
     // and are stored last; the (3,4)-type pairs are stored as soon as done.
@@ -407,7 +445,7 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
     for (int pi = 0; pi < kDirs / 2; ++pi) {
       const int d = (2 * pi + 8) % kDirs;
       R Rp[4], Rn[4], omp, omn;
-      pair_cubics<R, FORCE>(d, c, nT, nmT, gt, gux, guy, Fx, Fy, Rp, Rn, omp, omn);
+      pair_cubics<R, FORCE != 0>(d, c, nT, nmT, gt, gux, guy, Fx, Fy, Rp, Rn, omp, omn);
       const int kind = dir_kind(d);
       if constexpr (Park<R>::kOn) {
         park_load(park + d * park_stride, &f[4 * d]);
@@ -443,7 +481,7 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
       }
     }
     if (kProject) {
-      if (FORCE) {
+      if (FORCE != 0) {
         // forcing changes T^0a by (F.N_E, F N_E^0), N_E = n gamma (1, u)
         const R nG = (R(1) + M.dn) * M.gamma;
         rE -= nG * (Fx * M.ux + Fy * M.uy);
@@ -478,21 +516,26 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
 }
 
 // Fused stream + collide of site (x, y) (nothing if x >= nx).
-template <typename S, bool FORCE, int RES, class C>
+template <typename S, int FORCE, int RES, class C>
 __device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restrict__ fout,
                                           const DevSample& s, int x, int y,
                                           const typename Codec<S>::R* __restrict__ ghost,
                                           const StepAux<typename Codec<S>::R>& aux, const C& qc,
-                                          double& r_du2, double& r_u2, uint32_t park) {
+                                          double& r_du2, double& r_u2, uint32_t park, int cur) {
+  using R = typename Codec<S>::R;
   if (x < s.nx) {
-    typename Codec<S>::R f[kQ];
+    R f[kQ];
     gather(fin, s, x, y, ghost, qc, DirectSrc(), f);
-    collide_store<S, FORCE, RES>(f, fout, s, x, y, aux, qc, r_du2, r_u2, park);
+    // select, not s.dn[cur]: a runtime index would move the descriptor to local memory
+    void* const prev = cur ? s.dn[1] : s.dn[0];
+    void* const next = cur ? s.dn[0] : s.dn[1];
+    collide_store<S, FORCE, RES>(f, fout, s, x, y, aux, qc, r_du2, r_u2, park,
+                                 static_cast<const R*>(prev), static_cast<R*>(next));
   }
 }
 
 // One sample, one block row of kBX sites.
-template <typename S, bool FORCE, int RES, class C>
+template <typename S, int FORCE, int RES, class C>
 __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restrict__ fout,
                                           const DevSample& s,
                                           const typename Codec<S>::R* __restrict__ ghost,
@@ -500,7 +543,7 @@ __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restri
                                           unsigned char* park) {
   double r_du2 = 0.0, r_u2 = 0.0;
   site_step<S, FORCE, RES>(fin, fout, s, blockIdx.x * kBX + threadIdx.x, blockIdx.y, ghost, aux,
-                           qc, r_du2, r_u2, smem_addr(park) + threadIdx.x * 16u);
+                           qc, r_du2, r_u2, smem_addr(park) + threadIdx.x * 16u, s.cur);
   if (RES == 2) block_reduce_add2<typename Codec<S>::R>(r_du2, r_u2, aux.acc);
 }
 
@@ -518,7 +561,7 @@ struct BatchArgs {
   long long ntiles;
 };
 
-template <typename S, bool FORCE, int RES, int BX, class C>
+template <typename S, int FORCE, int RES, int BX, class C>
 __device__ __forceinline__ void batch_body(S* __restrict__ base, const BatchArgs& b,
                                            const typename Codec<S>::R* __restrict__ ghost,
                                            const StepAux<typename Codec<S>::R>& aux, const C& qc,
@@ -541,7 +584,7 @@ __device__ __forceinline__ void batch_body(S* __restrict__ base, const BatchArgs
     double r_du2 = 0.0, r_u2 = 0.0;
     site_step<S, FORCE, RES>(base + oin, base + oout, s, x, y,
                              ghost + (long long)lo * kMaxContacts * kQ, aux, qc, r_du2, r_u2,
-                             my_park);
+                             my_park, b.cur);
     // per-sample residual accumulators: acc[2 k], acc[2 k + 1]
     if (RES == 2) {
       block_reduce_add2<typename Codec<S>::R>(r_du2, r_u2, aux.acc + 2 * lo);
@@ -562,7 +605,7 @@ __device__ __forceinline__ void batch_body(S* __restrict__ base, const BatchArgs
 // (about 1 s): a warp that gives up sets kErrTimeout and a shared abort flag,
 // waits once more (bounded) for the copies of both buffers, and leaves the
 // loop; the other warps leave at their next tile.
-template <typename S, bool FORCE, int RES, int BX, class C>
+template <typename S, int FORCE, int RES, int BX, class C>
 __device__ __forceinline__ void staged_batch_body(S* __restrict__ base, const BatchArgs& b,
                                                   const typename Codec<S>::R* __restrict__ ghost,
                                                   const StepAux<typename Codec<S>::R>& aux,
@@ -658,7 +701,9 @@ __device__ __forceinline__ void staged_batch_body(S* __restrict__ base, const Ba
     double r_du2 = 0.0, r_u2 = 0.0;
     if (x < s.nx)
       collide_store<S, FORCE, RES>(f, base + (b.cur ? s.off[0] : s.off[1]), s, x, tl.z, aux, qc,
-                                   r_du2, r_u2, my_park);
+                                   r_du2, r_u2, my_park,
+                                   static_cast<const R*>(b.cur ? s.dn[1] : s.dn[0]),
+                                   static_cast<R*>(b.cur ? s.dn[0] : s.dn[1]));
     if (RES == 2) warp_reduce_add2(r_du2, r_u2, aux.acc + 2 * tl.x);
     t += G;
     if (t >= b.ntiles) break;
@@ -670,7 +715,8 @@ template <typename S, class C>
 __device__ __forceinline__ void moments_body(const S* __restrict__ fin, const DevSample& s,
                                              const typename Codec<S>::R* __restrict__ ghost,
                                              double* n, double* ux, double* uy, double* T,
-                                             unsigned* err, const C& qc) {
+                                             unsigned* err, const C& qc,
+                                             typename Codec<S>::R* dn_out) {
   using R = typename Codec<S>::R;
   const int bx0 = blockIdx.x * kBX;
   const int x = bx0 + threadIdx.x;
@@ -689,6 +735,7 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ fin, const De
   if (ux) ux[k] = double(M.ux);
   if (uy) uy[k] = double(M.uy);
   if (T) T[k] = 1.0 + double(M.dT);
+  if (dn_out) dn_out[(long long)y * s.ldx + x] = M.dn;
 }
 
 // Stored state := f^eq(n, u, T) - w (dense FP64 inputs).
@@ -719,6 +766,8 @@ __device__ __forceinline__ void init_body(S* __restrict__ fout, const DevSample&
   const R nT = (R(1) + M.dn) * inv1T;
   const R nmT = (M.dn - M.dT) * inv1T;
   const long long site = (long long)y * s.ldx + x;
+  void* const dn0 = s.cur ? s.dn[1] : s.dn[0];
+  if (dn0) static_cast<R*>(dn0)[site] = M.dn;     // the electric force's first step
 #pragma unroll
   for (int d = 0; d < kDirs; d += 2) {
     R Rp[4], Rn[4], omp, omn;

@@ -31,7 +31,7 @@ constexpr int kStepRegs = (65536 / (RLBM_STEP_MIN_BLOCKS * kBX)) > 255
 
 // Dynamic shared memory of the direct step kernels: the parking area
 // (park_bytes: 12 x threads x 16 B with FP32 arithmetic, none with FP64).
-template <bool FORCE, int RES>
+template <int FORCE, int RES>
 __global__ void __maxnreg__(kStepRegs) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                               DevSample s, const R* __restrict__ ghost,
                                               StepAux<R> aux) {
@@ -39,7 +39,7 @@ __global__ void __maxnreg__(kStepRegs) k_step(const S* __restrict__ fin, S* __re
   step_body<S, FORCE, RES>(fin, fout, s, ghost, aux, c_qc, park_smem);
 }
 
-template <bool FORCE, int RES, int BX>
+template <int FORCE, int RES, int BX>
 __global__ void __maxnreg__(kStepRegs)
 k_step_batch(S* __restrict__ base, BatchArgs b, const R* __restrict__ ghost, StepAux<R> aux) {
   extern __shared__ __align__(128) unsigned char park_smem[];
@@ -47,7 +47,7 @@ k_step_batch(S* __restrict__ base, BatchArgs b, const R* __restrict__ ghost, Ste
 }
 
 // Staged pulls (persistent; dynamic shared memory: two slot-row buffers).
-template <bool FORCE, int RES, int BX>
+template <int FORCE, int RES, int BX>
 __global__ void __maxnreg__(kStepRegs)
 k_step_staged(S* __restrict__ base, BatchArgs b, const R* __restrict__ ghost, StepAux<R> aux) {
   extern __shared__ __align__(128) unsigned char stage_smem[];
@@ -61,20 +61,23 @@ cudaError_t allow_stage_smem() {
   auto set = [&](const void* fn) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   };
-  set((const void*)k_step_staged<true, 0, BX>);
-  set((const void*)k_step_staged<true, 1, BX>);
-  set((const void*)k_step_staged<true, 2, BX>);
-  set((const void*)k_step_staged<false, 0, BX>);
-  set((const void*)k_step_staged<false, 1, BX>);
-  set((const void*)k_step_staged<false, 2, BX>);
+  set((const void*)k_step_staged<0, 0, BX>);
+  set((const void*)k_step_staged<0, 1, BX>);
+  set((const void*)k_step_staged<0, 2, BX>);
+  set((const void*)k_step_staged<1, 0, BX>);
+  set((const void*)k_step_staged<1, 1, BX>);
+  set((const void*)k_step_staged<1, 2, BX>);
+  set((const void*)k_step_staged<2, 0, BX>);
+  set((const void*)k_step_staged<2, 1, BX>);
+  set((const void*)k_step_staged<2, 2, BX>);
   return e;
 }
 
 __global__ void __launch_bounds__(kBX) k_moments(const S* __restrict__ fin, DevSample s,
                                                  const R* __restrict__ ghost, double* n,
                                                  double* ux, double* uy, double* T,
-                                                 unsigned* err) {
-  moments_body<S>(fin, s, ghost, n, ux, uy, T, err, c_qc);
+                                                 unsigned* err, R* dn_out) {
+  moments_body<S>(fin, s, ghost, n, ux, uy, T, err, c_qc, dn_out);
 }
 
 __global__ void __launch_bounds__(kBX) k_init(S* __restrict__ fout, DevSample s, const double* n,
@@ -124,55 +127,54 @@ cudaError_t upload(const double p0[4], const double w[2][4], double scale) {
   return e;
 }
 
-cudaError_t step(const void* fin, void* fout, const DevSample& s, const void* ghost, bool force,
+template <int F>
+void launch_single(const S* a, S* b, const DevSample& s, const R* g, int res, const StepAux<R>& aux,
+                   cudaStream_t st) {
+  const dim3 grid = site_grid(s);
+  const size_t pk = park_bytes<R>(kBX);
+  if (res == 0) k_step<F, 0><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
+  else if (res == 1) k_step<F, 1><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
+  else k_step<F, 2><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
+}
+
+cudaError_t step(const void* fin, void* fout, const DevSample& s, const void* ghost, int force,
                  int res, void* uprev, double* acc, unsigned* err, cudaStream_t st) {
   StepAux<R> aux{static_cast<R*>(uprev), acc, err};
   const S* a = static_cast<const S*>(fin);
   S* b = static_cast<S*>(fout);
   const R* g = static_cast<const R*>(ghost);
-  const dim3 grid = site_grid(s);
-  const size_t pk = park_bytes<R>(kBX);
-  if (force) {
-    if (res == 0) k_step<true, 0><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
-    else if (res == 1) k_step<true, 1><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
-    else k_step<true, 2><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
-  } else {
-    if (res == 0) k_step<false, 0><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
-    else if (res == 1) k_step<false, 1><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
-    else k_step<false, 2><<<grid, kBX, pk, st>>>(a, b, s, g, aux);
-  }
+  if (force == kForceLca) launch_single<kForceLca>(a, b, s, g, res, aux, st);
+  else if (force == kForceUniform) launch_single<kForceUniform>(a, b, s, g, res, aux, st);
+  else launch_single<kForceNone>(a, b, s, g, res, aux, st);
   return cudaGetLastError();
 }
 
-template <int BX>
-void launch_batch(S* base, const BatchArgs& b, const R* g, bool force, int res, int grid,
-                  int staged, const StepAux<R>& aux, cudaStream_t st) {
+template <int F, int BX>
+void launch_batch_f(S* base, const BatchArgs& b, const R* g, int res, int grid, int staged,
+                    const StepAux<R>& aux, cudaStream_t st) {
   if (staged == 1) {
     const size_t sm = Stage<S>::template smem_bytes<BX>();
-    if (force) {
-      if (res == 0) k_step_staged<true, 0, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
-      else if (res == 1) k_step_staged<true, 1, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
-      else k_step_staged<true, 2, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
-    } else {
-      if (res == 0) k_step_staged<false, 0, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
-      else if (res == 1) k_step_staged<false, 1, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
-      else k_step_staged<false, 2, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
-    }
+    if (res == 0) k_step_staged<F, 0, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
+    else if (res == 1) k_step_staged<F, 1, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
+    else k_step_staged<F, 2, BX><<<grid, BX, sm, st>>>(base, b, g, aux);
     return;
   }
   const size_t pk = park_bytes<R>(BX);
-  if (force) {
-    if (res == 0) k_step_batch<true, 0, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
-    else if (res == 1) k_step_batch<true, 1, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
-    else k_step_batch<true, 2, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
-  } else {
-    if (res == 0) k_step_batch<false, 0, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
-    else if (res == 1) k_step_batch<false, 1, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
-    else k_step_batch<false, 2, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
-  }
+  if (res == 0) k_step_batch<F, 0, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
+  else if (res == 1) k_step_batch<F, 1, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
+  else k_step_batch<F, 2, BX><<<grid, BX, pk, st>>>(base, b, g, aux);
 }
 
-cudaError_t step_batch(void* base, const BatchArgs& b, const void* ghost, bool force, int res,
+template <int BX>
+void launch_batch(S* base, const BatchArgs& b, const R* g, int force, int res, int grid,
+                  int staged, const StepAux<R>& aux, cudaStream_t st) {
+  if (force == kForceLca) launch_batch_f<kForceLca, BX>(base, b, g, res, grid, staged, aux, st);
+  else if (force == kForceUniform)
+    launch_batch_f<kForceUniform, BX>(base, b, g, res, grid, staged, aux, st);
+  else launch_batch_f<kForceNone, BX>(base, b, g, res, grid, staged, aux, st);
+}
+
+cudaError_t step_batch(void* base, const BatchArgs& b, const void* ghost, int force, int res,
                        int bx, int grid, int staged, void* uprev, double* acc, unsigned* err,
                        cudaStream_t st) {
   StepAux<R> aux{static_cast<R*>(uprev), acc, err};
@@ -185,9 +187,10 @@ cudaError_t step_batch(void* base, const BatchArgs& b, const void* ghost, bool f
 }
 
 cudaError_t moments(const void* fin, const DevSample& s, const void* ghost, double* n, double* ux,
-                    double* uy, double* T, unsigned* err, cudaStream_t st) {
+                    double* uy, double* T, unsigned* err, void* dn_out, cudaStream_t st) {
   k_moments<<<site_grid(s), kBX, 0, st>>>(static_cast<const S*>(fin), s,
-                                         static_cast<const R*>(ghost), n, ux, uy, T, err);
+                                         static_cast<const R*>(ghost), n, ux, uy, T, err,
+                                         static_cast<R*>(dn_out));
   return cudaGetLastError();
 }
 

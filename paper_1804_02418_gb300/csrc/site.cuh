@@ -63,6 +63,13 @@ struct DevSample {
   double inv_tau;
   double Fx, Fy;
   int cedge[kMaxContacts], clo[kMaxContacts], chi[kMaxContacts];
+  // electric force of the local capacitance approximation (Sec. 3): coupling
+  // e^2 / C_g (0: none) and two planes of n - 1 in the arithmetic type, same
+  // site indexing as a population plane; dn[cur] holds the previous step's
+  // density, dn[cur ^ 1] receives this step's
+  double inv_cg;
+  void* dn[2];
+  int cur;
 };
 
 // Error bits of the device error word.

@@ -39,7 +39,8 @@ class _Sample(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int),
                 ("tau", ctypes.c_double), ("Fx", ctypes.c_double), ("Fy", ctypes.c_double),
-                ("ncontacts", ctypes.c_int), ("contacts", _Contact * 4)]
+                ("ncontacts", ctypes.c_int), ("contacts", _Contact * 4),
+                ("inv_cg", ctypes.c_double)]
 
 
 class _Config(ctypes.Structure):
@@ -107,6 +108,7 @@ def _to_c_sample(s: workloads.Sample) -> _Sample:
     c.nx, c.ny = int(s.nx), int(s.ny)
     c.periodic_x, c.periodic_y = int(bool(s.periodic_x)), int(bool(s.periodic_y))
     c.tau, c.Fx, c.Fy = float(s.tau), float(s.Fx), float(s.Fy)
+    c.inv_cg = float(getattr(s, "inv_cg", 0.0))
     c.ncontacts = len(s.contacts)
     if c.ncontacts > 4:
         raise ValueError("at most 4 contacts per sample")

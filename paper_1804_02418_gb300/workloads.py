@@ -51,6 +51,8 @@ class Sample:
     Fx: float = 0.0
     Fy: float = 0.0
     contacts: List[Contact] = field(default_factory=list)
+    # electric force of the local capacitance approximation: e^2 / C_g (0: none)
+    inv_cg: float = 0.0
 
     @property
     def sites(self) -> int:
