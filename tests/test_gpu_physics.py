@@ -8,6 +8,12 @@
   beside the injector.
 * Viscosity: the transverse shear wave decays at nu k^2 with
   nu = (tau - 1/2) c^2 / 4, c = 5 sites per step (within 1 % at 64^2).
+* Potential near an injector (Sec. 3, Eq. phi-approx-inlet): on circles
+  about a point injector on a no-slip edge, the potential per particle is
+  A(r) cos(2 theta) + const with r^2 A = -2 I eta / (pi n^2) (Stokes flow
+  from a wall source): fitted per circle at r = 40, 60, 80 sites, the
+  cos(2 theta) shape within 8 % rms, r^2 A within [0.85, 1.05] of the law
+  and the three circles within 8 % of each other (collapse).
 """
 import numpy as np
 import pytest
@@ -86,3 +92,19 @@ def test_shear_wave_viscosity_on_gpu(rl):
     rate = -np.polyfit(t[1:], np.log(amps[1:]), 1)[0]
     nu = (tau - 0.5) * 25.0 / 4.0
     assert abs(rate / (nu * (2 * np.pi / n) ** 2) - 1.0) < 0.01
+
+
+def test_injector_potential_follows_the_stokes_law(rl):
+    from paper_1804_02418_gb300 import injector as J
+    n0 = T0 = 1.0
+    s = J.geometry(600, 300, 8, 1e-4, n0, T0, 0.8, 0.1)
+    fields, steps, r = J.steady(s, n0, T0, "f32", 1e-8, max_steps=200000, chunk=10000)
+    U, I = J.potential(s, fields, n0, T0)
+    th, prof, fits, eta, pred = J.analyse(s, U, I, n0, T0, radii=(40, 60, 80))
+    ratio = {k: (k / 5.0) ** 2 * f[0] / pred for k, f in fits.items()}
+    print("injector: steps", steps, "residual", r, "r^2 A / law", ratio,
+          "rms / A", {k: f[2] for k, f in fits.items()})
+    for k, f in fits.items():
+        assert f[2] < 0.08, (k, f)
+        assert 0.85 < ratio[k] < 1.05, (k, ratio[k])
+    assert max(ratio.values()) - min(ratio.values()) < 0.08
