@@ -180,7 +180,10 @@ int rlbm_moments(rlbm_ctx* ctx, int sample, double* n, double* ux, double* uy,
                  double* T, int device_ptrs);
 
 /* Stored post-collision state of `sample` as deviations f_i - w_i, layout
- * [48][ny][nx] FP64 (checkpoint / restart and one-step checks).  With the
+ * [48][ny][nx] FP64 (checkpoint / restart and one-step checks).  The library
+ * stores relative deviations (f_i - w_i) / w_i and converts in FP64: a
+ * get / set round trip is exact for FP32 and 16-bit storage and within one
+ * ulp for FP64 storage.  With the
  * electric force on, rlbm_set_state also sets the density the next step's
  * force uses, to the density of the restored state (the previous step's
  * density is not part of the checkpoint). */

@@ -35,7 +35,7 @@ struct SampleLayout {
   size_t dn_off[2];      // byte offsets of the two density planes (electric force only)
   size_t dn_bytes;       // 0 without the electric force
   long long sites;
-  double ghost[kMaxContacts][kQ];   // contact deviations f^eq - w
+  double ghost[kMaxContacts][kQ];   // contact relative deviations (f^eq - w) / w
 };
 
 struct Quad {

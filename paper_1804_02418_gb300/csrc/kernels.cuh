@@ -1,5 +1,8 @@
 // Kernels of the fused relativistic LBM step, templated on the storage type.
 //
+// Stored values are relative deviations g = (f - w) / w from the rest weights
+// (times s in 16-bit storage).
+//
 // Layout in HBM (per sample): two ping-pong buffers, each 12 direction planes
 // of `plane` sites (row-major, row pitch ldx a multiple of 32, plane a
 // multiple of 64 sites).  A site of direction plane d holds the four shells of
@@ -319,8 +322,9 @@ __device__ __forceinline__ void warp_reduce_add2(double a, double b, double* acc
   }
 }
 
-// New deviations of the four shells of a direction from its cubic:
-// out_j = (1 - omega) f_j + w_j (R0 + R1 p0_j + R2 p0_j^2 + R3 p0_j^3).
+// New relative deviations of the four shells of a direction from its cubic:
+// out_j = (1 - omega) g_j + R0 + R1 p0_j + R2 p0_j^2 + R3 p0_j^3
+// (delta = w g: the weight w_j drops out of the update).
 template <typename R, class C>
 __device__ __forceinline__ void relax_shells(const R (&Rm)[4], R omega, int kind, const C& qc,
                                              R* f) {
@@ -329,18 +333,20 @@ __device__ __forceinline__ void relax_shells(const R (&Rm)[4], R omega, int kind
   for (int j = 0; j < kShells; ++j) {
     const R p = qc.p0[j];
     const R val = fma(fma(fma(Rm[3], p, Rm[2]), p, Rm[1]), p, Rm[0]);
-    f[j] = fma(qc.w[kind][j], val, omc * f[j]);
+    f[j] = fma(omc, f[j], val);
   }
 }
 
-// Adds sum_j (out_j - in_j) p0_j and sum_j (out_j - in_j) p0_j^2 of one direction.
+// Adds sum_j w_j (out_j - in_j) p0_j and sum_j w_j (out_j - in_j) p0_j^2 of one
+// direction (relative deviations in / out).
 template <typename R, class C>
-__device__ __forceinline__ void balance(const R* in, const R* out, const C& qc, R& aN, R& aE) {
+__device__ __forceinline__ void balance(const R* in, const R* out, int kind, const C& qc, R& aN,
+                                        R& aE) {
 #pragma unroll
   for (int j = 0; j < kShells; ++j) {
     const R dlt = out[j] - in[j];
-    aN = fma(dlt, qc.p0[j], aN);
-    aE = fma(dlt, qc.p0sq[j], aE);
+    aN = fma(dlt, qc.wp0[kind][j], aN);
+    aE = fma(dlt, qc.wp0sq[kind][j], aE);
   }
 }
 
@@ -458,8 +464,8 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
         relax_shells(Rp, omp, kind, qc, &f[4 * d]);
         relax_shells(Rn, omn, kind, qc, &f[4 * d + 4]);
         R aNp = R(0), aEp = R(0), aNn = R(0), aEn = R(0);
-        balance(in, &f[4 * d], qc, aNp, aEp);
-        balance(in + 4, &f[4 * d + 4], qc, aNn, aEn);
+        balance(in, &f[4 * d], kind, qc, aNp, aEp);
+        balance(in + 4, &f[4 * d + 4], kind, qc, aNn, aEn);
         rN += aNp + aNn;
         rE += aEp + aEn;
         const R vx = R(hop_x(d)) / R(5), vy = R(hop_y(d)) / R(5);
@@ -497,7 +503,7 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
         if constexpr (Park<R>::kOn) park_load(park + d * park_stride, &f[4 * d]);
 #pragma unroll
         for (int j = 0; j < kShells; ++j)
-          f[4 * d + j] = fma(qc.w[1][j], fma(qc.p0[j], cd, l0), f[4 * d + j]);
+          f[4 * d + j] = f[4 * d + j] + fma(qc.p0[j], cd, l0);   // delta += w (l0 + p0 cd)
         Codec<S>::store4(fout + vec_index(s, d, site), 1, qc, &f[4 * d]);
       }
     }
@@ -793,7 +799,7 @@ __device__ __forceinline__ void get_state_body(const S* __restrict__ fin, const 
   if (x >= s.nx) return;
   const int d = q >> 2, j = q & 3;
   const S v = fin[vec_index(s, d, (long long)y * s.ldx + x) + j];
-  out[((long long)dq * s.ny + y) * s.nx + x] = double(Codec<S>::decode(v, dir_kind(d), j, qc));
+  out[((long long)dq * s.ny + y) * s.nx + x] = Codec<S>::decode(v, dir_kind(d), j, qc);
 }
 
 template <typename S, class C>
@@ -806,8 +812,7 @@ __device__ __forceinline__ void set_state_body(S* __restrict__ fout, const DevSa
   if (x >= s.nx) return;
   const int d = q >> 2, j = q & 3;
   const double v = in[((long long)dq * s.ny + y) * s.nx + x];
-  fout[vec_index(s, d, (long long)y * s.ldx + x) + j] =
-      Codec<S>::encode(R(v), dir_kind(d), j, qc);
+  fout[vec_index(s, d, (long long)y * s.ldx + x) + j] = Codec<S>::encode(v, dir_kind(d), j, qc);
 }
 
 }  // namespace rlbm

@@ -101,13 +101,15 @@ dim3 site_grid(const DevSample& s) { return dim3((s.nx + kBX - 1) / kBX, s.ny, 1
 cudaError_t upload(const double p0[4], const double w[2][4], double scale) {
   QuadConsts<R> h;
   double K[4] = {0.0, 0.0, 0.0, 0.0};     // K_m = sum_j w_2j p0_j^m
+  h.dec_s = R(1.0 / scale);
+  h.enc_s = R(scale);
   for (int j = 0; j < kShells; ++j) {
     h.p0[j] = R(p0[j]);
-    h.p0sq[j] = R(p0[j] * p0[j]);
     for (int k = 0; k < 2; ++k) {
       h.w[k][j] = R(w[k][j]);
-      h.dec[k][j] = R(w[k][j] / scale);
-      h.enc[k][j] = R(scale / w[k][j]);
+      h.wd[k][j] = w[k][j];
+      h.wp0[k][j] = R(w[k][j] * p0[j]);
+      h.wp0sq[k][j] = R(w[k][j] * p0[j] * p0[j]);
     }
     for (int m = 1; m <= 3; ++m) K[m] += w[1][j] * std::pow(p0[j], m);
   }

@@ -1,9 +1,11 @@
 // Per-site arithmetic of the relativistic lattice Boltzmann step
 // (Eq. discrete-rbe, the per-site algorithm at the end of Sec. 2, App. A-B).
 //
-// Everything here works on deviations from the rest equilibrium
-// (n = T = 1, u = 0, where f^eq_i = w_i):  delta_i = f_i - w_i.  Rest values of
-// the moments (N = (1,0,0), T = diag(2,1,1)) are added analytically, and the
+// Everything here works on relative deviations from the rest equilibrium
+// (n = T = 1, u = 0, where f^eq_i = w_i):  g_i = (f_i - w_i) / w_i, the value
+// every storage type keeps (16-bit storage scaled by s); delta_i = w_i g_i.
+// Rest values of the moments (N = (1,0,0), T = diag(2,1,1)) are added
+// analytically, and the
 // equilibrium coefficients are written in terms of the small quantities
 // n - 1, T - 1, gamma - 1 and T gamma - 1, so FP32 arithmetic keeps full
 // relative precision on the O(u) flux-carrying parts.
@@ -42,10 +44,11 @@ __host__ __device__ constexpr int dir_kind(int d) { return d < 8 ? 0 : 1; }
 template <typename R>
 struct QuadConsts {
   R p0[kShells];            // shell energies p0_j
-  R p0sq[kShells];          // p0_j^2
   R w[2][kShells];          // weights by direction kind and shell
-  R dec[2][kShells];        // 16-bit storage: delta = g * dec  (dec = w / s)
-  R enc[2][kShells];        // 16-bit storage: g = delta * enc  (enc = s / w)
+  R wp0[2][kShells];        // w p0_j   (moments of relative deviations)
+  R wp0sq[2][kShells];      // w p0_j^2
+  R dec_s, enc_s;           // 16-bit storage of s g: g = h * dec_s (1 / s), h = g * enc_s (s)
+  double wd[2][kShells];    // w in FP64: state I/O converts g <-> delta = w g in FP64
   // Conservation projection (reduced precision): correction
   // w_2j (l0 + l1 p0_j + p0_j (lx vx + ly vy)) on the (5,0)-type directions,
   // (l0, l1) = P (rN, rE), (lx, ly) = px (rX, rY).
@@ -104,8 +107,14 @@ template <> struct Codec<double> {
     reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
     reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
   }
-  template <class C> __device__ static R decode(double v, int, int, const C&) { return v; }
-  template <class C> __device__ static double encode(R v, int, int, const C&) { return v; }
+  // stored relative deviation g <-> deviation delta = f - w (state I/O, in
+  // FP64; the round trip can move a value by one ulp)
+  template <class C> __device__ static double decode(double v, int kind, int j, const C& c) {
+    return v * c.wd[kind][j];
+  }
+  template <class C> __device__ static double encode(double v, int kind, int j, const C& c) {
+    return v / c.wd[kind][j];
+  }
 };
 template <> struct Codec<float> {
   using R = float;
@@ -123,8 +132,13 @@ template <> struct Codec<float> {
   __device__ static void store4(float* p, int, const C&, const R* v) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   }
-  template <class C> __device__ static R decode(float v, int, int, const C&) { return v; }
-  template <class C> __device__ static float encode(R v, int, int, const C&) { return v; }
+  // in FP64: delta = g w to 1e-16, and delta / w rounds back to g exactly
+  template <class C> __device__ static double decode(float v, int kind, int j, const C& c) {
+    return double(v) * c.wd[kind][j];
+  }
+  template <class C> __device__ static float encode(double v, int kind, int j, const C& c) {
+    return float(v / c.wd[kind][j]);
+  }
 };
 template <typename H> struct Codec16 {
   using R = float;
@@ -136,7 +150,7 @@ template <typename H> struct Codec16 {
     H h[4];
     memcpy(h, &u, sizeof u);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]) * c.dec[kind][j];
+    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]) * c.dec_s;
   }
   template <class C>
   __device__ static void load4s(uint32_t a, int kind, const C& c, R* o) {
@@ -145,22 +159,23 @@ template <typename H> struct Codec16 {
     H h[4];
     memcpy(h, &u, sizeof u);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]) * c.dec[kind][j];
+    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]) * c.dec_s;
   }
   template <class C>
   __device__ static void store4(H* p, int kind, const C& c, const R* v) {
     H h[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) h[j] = fromf(v[j] * c.enc[kind][j]);
+    for (int j = 0; j < 4; ++j) h[j] = fromf(v[j] * c.enc_s);
     uint2 u;
     memcpy(&u, h, sizeof u);
     *reinterpret_cast<uint2*>(p) = u;
   }
-  template <class C> __device__ static R decode(H v, int kind, int j, const C& c) {
-    return tof(v) * c.dec[kind][j];
+  // stored s g <-> deviation delta = f - w (state I/O, in FP64: exact round trip)
+  template <class C> __device__ static double decode(H v, int kind, int j, const C& c) {
+    return double(tof(v)) * double(c.dec_s) * c.wd[kind][j];
   }
-  template <class C> __device__ static H encode(R v, int kind, int j, const C& c) {
-    return fromf(v * c.enc[kind][j]);
+  template <class C> __device__ static H encode(double v, int kind, int j, const C& c) {
+    return fromf(float(v / c.wd[kind][j] * double(c.enc_s)));
   }
 };
 template <> __device__ inline float Codec16<__half>::tof(__half h) { return __half2float(h); }
@@ -210,10 +225,12 @@ __device__ __forceinline__ Moments<R> moments(const R (&f)[kQ], const C& qc) {
     R Ap = R(0), Bp = R(0), An = R(0), Bn = R(0);
 #pragma unroll
     for (int j = 0; j < kShells; ++j) {
-      Ap = fma(f[4 * d + j], qc.p0[j], Ap);
-      Bp = fma(f[4 * d + j], qc.p0sq[j], Bp);
-      An = fma(f[4 * d + 4 + j], qc.p0[j], An);
-      Bn = fma(f[4 * d + 4 + j], qc.p0sq[j], Bn);
+      // relative deviations: delta = w g
+      const int k = dir_kind(d);
+      Ap = fma(f[4 * d + j], qc.wp0[k][j], Ap);
+      Bp = fma(f[4 * d + j], qc.wp0sq[k][j], Bp);
+      An = fma(f[4 * d + 4 + j], qc.wp0[k][j], An);
+      Bn = fma(f[4 * d + 4 + j], qc.wp0sq[k][j], Bn);
     }
     const R vx = R(hop_x(d)) / R(5), vy = R(hop_y(d)) / R(5);
     const R Ae = Ap + An, Ao = Ap - An, Be = Bp + Bn, Bo = Bp - Bn;
