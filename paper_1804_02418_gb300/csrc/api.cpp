@@ -306,8 +306,10 @@ int upload_ghosts(rlbm_ctx* c) {
                                     c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ghost copy");
   } else {
+    // 16-bit storage: the kernels compute on s g
+    const double sc = storage_scale(c->prec);
     std::vector<float> gf(ghost.size());
-    for (size_t i = 0; i < ghost.size(); ++i) gf[i] = (float)ghost[i];
+    for (size_t i = 0; i < ghost.size(); ++i) gf[i] = (float)(ghost[i] * sc);
     cudaError_t e = cudaMemcpyAsync(at<float>(c, c->ghost_off), gf.data(),
                                     gf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

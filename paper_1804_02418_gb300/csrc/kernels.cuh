@@ -1,7 +1,7 @@
 // Kernels of the fused relativistic LBM step, templated on the storage type.
 //
 // Stored values are relative deviations g = (f - w) / w from the rest weights
-// (times s in 16-bit storage).
+// (times s in 16-bit storage, where the kernels also compute on s g).
 //
 // Layout in HBM (per sample): two ping-pong buffers, each 12 direction planes
 // of `plane` sites (row-major, row pitch ldx a multiple of 32, plane a
@@ -435,9 +435,12 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
     if (bad) atomicOr(aux.err, bad);
 
     const EqCoeffs<R> c = eq_coeffs(M);
+    // every term of the update is proportional to n/T or (n - T)/T: the
+    // 16-bit kernels, which work on the stored s g, scale those by s
+    const R scl = sizeof(S) == 2 ? qc.enc_s : R(1);
     const R inv1T = qdiv(R(1), R(1) + M.dT);
-    const R nT = (R(1) + M.dn) * inv1T;
-    const R nmT = (M.dn - M.dT) * inv1T;
+    const R nT = (R(1) + M.dn) * inv1T * scl;
+    const R nmT = (M.dn - M.dT) * inv1T * scl;
     const R gt = M.gamma * R(s.inv_tau);
     const R gux = gt * M.ux, guy = gt * M.uy;
     const R Fx = lca ? R(s.Fx) + (-R(s.inv_cg) * egx) : R(s.Fx);
@@ -768,9 +771,10 @@ __device__ __forceinline__ void init_body(S* __restrict__ fout, const DevSample&
   if (!(u2 < 1.0) || !(n[k] > 0.0) || !(T[k] > 0.0) || !isfinite(n[k]) || !isfinite(T[k]))
     atomicOr(err, kErrUnphysical);
   const EqCoeffs<R> c = eq_coeffs(M);
+  const R scl = sizeof(S) == 2 ? qc.enc_s : R(1);     // 16-bit storage holds s g
   const R inv1T = R(1) / (R(1) + M.dT);
-  const R nT = (R(1) + M.dn) * inv1T;
-  const R nmT = (M.dn - M.dT) * inv1T;
+  const R nT = (R(1) + M.dn) * inv1T * scl;
+  const R nmT = (M.dn - M.dT) * inv1T * scl;
   const long long site = (long long)y * s.ldx + x;
   void* const dn0 = s.cur ? s.dn[1] : s.dn[0];
   if (dn0) static_cast<R*>(dn0)[site] = M.dn;     // the electric force's first step

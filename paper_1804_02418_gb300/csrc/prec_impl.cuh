@@ -108,8 +108,8 @@ cudaError_t upload(const double p0[4], const double w[2][4], double scale) {
     for (int k = 0; k < 2; ++k) {
       h.w[k][j] = R(w[k][j]);
       h.wd[k][j] = w[k][j];
-      h.wp0[k][j] = R(w[k][j] * p0[j]);
-      h.wp0sq[k][j] = R(w[k][j] * p0[j] * p0[j]);
+      h.wp0[k][j] = R(w[k][j] * p0[j] / scale);
+      h.wp0sq[k][j] = R(w[k][j] * p0[j] * p0[j] / scale);
     }
     for (int m = 1; m <= 3; ++m) K[m] += w[1][j] * std::pow(p0[j], m);
   }

@@ -45,9 +45,9 @@ template <typename R>
 struct QuadConsts {
   R p0[kShells];            // shell energies p0_j
   R w[2][kShells];          // weights by direction kind and shell
-  R wp0[2][kShells];        // w p0_j   (moments of relative deviations)
-  R wp0sq[2][kShells];      // w p0_j^2
-  R dec_s, enc_s;           // 16-bit storage of s g: g = h * dec_s (1 / s), h = g * enc_s (s)
+  R wp0[2][kShells];        // w p0_j / s   (moments of the stored s g; s = 1 above 16 bits)
+  R wp0sq[2][kShells];      // w p0_j^2 / s
+  R dec_s, enc_s;           // 16-bit storage scale: 1 / s, s (the 16-bit kernels compute on s g)
   double wd[2][kShells];    // w in FP64: state I/O converts g <-> delta = w g in FP64
   // Conservation projection (reduced precision): correction
   // w_2j (l0 + l1 p0_j + p0_j (lx vx + ly vy)) on the (5,0)-type directions,
@@ -150,7 +150,7 @@ template <typename H> struct Codec16 {
     H h[4];
     memcpy(h, &u, sizeof u);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]) * c.dec_s;
+    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]);     // s g: the kernels work scaled
   }
   template <class C>
   __device__ static void load4s(uint32_t a, int kind, const C& c, R* o) {
@@ -159,13 +159,13 @@ template <typename H> struct Codec16 {
     H h[4];
     memcpy(h, &u, sizeof u);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]) * c.dec_s;
+    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]);     // s g: the kernels work scaled
   }
   template <class C>
   __device__ static void store4(H* p, int kind, const C& c, const R* v) {
     H h[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) h[j] = fromf(v[j] * c.enc_s);
+    for (int j = 0; j < 4; ++j) h[j] = fromf(v[j]);
     uint2 u;
     memcpy(&u, h, sizeof u);
     *reinterpret_cast<uint2*>(p) = u;
