@@ -15,6 +15,10 @@ Modules:
   lbm         streaming with walls / contacts / periodic wrap, moments,
               Landau-frame solve, equilibrium, forcing, relaxation (Sec. 2,
               Eq. discrete-rbe, Sec. 3)
+  massive     the massive-particle variant (m = 5 T0, the 45-vector stencil
+              of Fig. m5-stencil): quadrature solve, Gram-Schmidt
+              polynomials, equilibrium, Landau frame with the massive
+              equation of state, forcing, walls (Sec. 2.3)
 
 Every function is pinned by tests/test_oracle_*.py against what the paper and
 the mathematics fix (continuum integrals, exact rational moment sums, closed
