@@ -50,7 +50,12 @@ under <f, g> = int omega f g d^2p / p0 (exact rational Gram matrix).
 Equilibrium (Eq. feq-expansion-discrete):
     f^eq_i = w_i sum_k a^(k) J^(k)(p_i),   a^(k) = int f_MJ J^(k) d^2p / p0,
     f_MJ = A exp(-p.U / T),   A = n / (2 pi T (m + T) exp(-m/T))  (N = n U).
-The moments of f_MJ are those of its rest frame, boosted by U.
+The moments of f_MJ are those of its rest frame, boosted by U.  Precision:
+the Gram-Schmidt coefficients reach 170 and the nodes' monomials 3e3, so the
+moments enter the projection as deviations from their rest values, formed in
+numpy longdouble, and J^(k)(p_i) is tabulated from the 60-digit solve; f^eq
+is then within ~4e-14 of a 40-digit evaluation (FP64 throughout would leave
+~1e-12).
 
 Equation of state (2-D massive ideal gas; the same rest integrals):
     P = n T,   eps = n (m^2 + 2 m T + 2 T^2) / (m + T),
@@ -281,28 +286,32 @@ def monomial_values(p):
     return np.array([p[0] ** a * p[1] ** b * p[2] ** c for (a, b, c) in MONOMIALS])
 
 
+def _gram_schmidt_decimal(G):
+    """Lower-triangular C = L^-1 with G = L L^T (Decimal, current context)."""
+    n = len(G)
+    D = decimal.Decimal
+    Gd = [[D(g.numerator) / D(g.denominator) for g in row] for row in G]
+    L = [[D(0)] * n for _ in range(n)]
+    for i in range(n):
+        for j in range(i + 1):
+            s = Gd[i][j] - sum(L[i][k] * L[j][k] for k in range(j))
+            L[i][j] = s.sqrt() if i == j else s / L[j][j]
+    C = [[D(0)] * n for _ in range(n)]
+    for col in range(n):
+        for i in range(n):
+            s = (D(1) if i == col else D(0)) - sum(L[i][k] * C[k][col] for k in range(i))
+            C[i][col] = s / L[i][i]
+    return C
+
+
 @lru_cache(maxsize=None)
 def polynomials():
     """(16, 16) lower-triangular C with J^(k) = sum_b C[k, b] MONOMIALS[b]:
     Gram-Schmidt (Cholesky of the exact Gram matrix, in 60 digits)."""
-    n = len(MONOMIALS)
     G = [[omega_moment(a1 + a2, b1 + b2, c1 + c2) for (a2, b2, c2) in MONOMIALS]
          for (a1, b1, c1) in MONOMIALS]
     with decimal.localcontext(_ctx()):
-        D = decimal.Decimal
-        Gd = [[D(g.numerator) / D(g.denominator) for g in row] for row in G]
-        L = [[D(0)] * n for _ in range(n)]
-        for i in range(n):
-            for j in range(i + 1):
-                s = Gd[i][j] - sum(L[i][k] * L[j][k] for k in range(j))
-                L[i][j] = s.sqrt() if i == j else s / L[j][j]
-        # C = L^-1 (forward substitution on the identity)
-        C = [[D(0)] * n for _ in range(n)]
-        for col in range(n):
-            for i in range(n):
-                s = (D(1) if i == col else D(0)) - sum(L[i][k] * C[k][col] for k in range(i))
-                C[i][col] = s / L[i][i]
-        return np.array([[float(x) for x in row] for row in C])
+        return np.array([[float(x) for x in row] for row in _gram_schmidt_decimal(G)])
 
 
 # ---------------------------------------------------------------------------
@@ -320,10 +329,11 @@ def temperature(n, eps):
 def _rest_tensor(order, n, T):
     """Rest-frame moments int f_MJ p^a1 .. p^a_order d^2p/p0 of f_MJ(n, T) as
     an array of shape (3,)*order + T.shape (components 0, x, y)."""
-    T = np.asarray(T, float)
+    T = np.asarray(T, np.longdouble)
+    n = np.asarray(n, np.longdouble)
     m = MASS
     A = n / (2 * np.pi * T * (m + T))                  # A exp(-m/T), the exp cancels
-    out = np.zeros((3,) * order + T.shape)
+    out = np.zeros((3,) * order + T.shape, np.longdouble)
     for idx in np.ndindex(*((3,) * order)):
         a = idx.count(0)
         b = idx.count(1)
@@ -337,18 +347,18 @@ def _rest_tensor(order, n, T):
             k = a + 2 * l
             s = T * sum(comb(k, j) * factorial(j) * m ** (k - j) * T ** j for j in range(k + 1))
             rad = rad + comb(h, l) * (-m * m) ** (h - l) * s
-        out[idx] = 2 * np.pi * A * rad * float(ang)
+        out[idx] = 2 * np.pi * A * rad * (np.longdouble(ang.numerator) / ang.denominator)
     return out
 
 
 def boost(ux, uy):
     """Lorentz boost Lambda^a_b taking the rest frame to velocity u: (3, 3, ...)."""
-    ux = np.asarray(ux, float)
-    uy = np.asarray(uy, float)
+    ux = np.asarray(ux, np.longdouble)
+    uy = np.asarray(uy, np.longdouble)
     u2 = ux * ux + uy * uy
-    g = 1.0 / np.sqrt(1.0 - u2)
-    k = g * g / (g + 1.0)                              # (gamma - 1) / u^2
-    L = np.empty((3, 3) + ux.shape)
+    g = 1 / np.sqrt(1 - u2)
+    k = g * g / (g + 1)                                # (gamma - 1) / u^2
+    L = np.empty((3, 3) + ux.shape, np.longdouble)
     L[0, 0] = g
     L[0, 1] = L[1, 0] = g * ux
     L[0, 2] = L[2, 0] = g * uy
@@ -359,33 +369,78 @@ def boost(ux, uy):
 
 
 def mj_monomial_moments(n, ux, uy, T):
-    """(16, ...) int f_MJ m_b(p) d^2p/p0 for the MONOMIALS, f_MJ(n, U, T)."""
+    """(16, ...) int f_MJ m_b(p) d^2p/p0 for the MONOMIALS, f_MJ(n, U, T), in
+    numpy longdouble: the component of the boosted rest-frame tensor,
+        M^{a1..ak} = Lambda^a1_d1 .. Lambda^ak_dk R^{d1..dk}."""
     L = boost(ux, uy)
-    R0 = _rest_tensor(0, n, T)
-    M1 = np.einsum("ab...,b...->a...", L, _rest_tensor(1, n, T))
-    M2 = np.einsum("ac...,bd...,cd...->ab...", L, L, _rest_tensor(2, n, T))
-    M3 = np.einsum("ad...,be...,cf...,def...->abc...", L, L, L, _rest_tensor(3, n, T))
-    tensors = {0: R0, 1: M1, 2: M2, 3: M3}
+    R = [_rest_tensor(k, n, T) for k in range(4)]
     out = []
     for (a, b, c) in MONOMIALS:
         idx = (0,) * a + (1,) * b + (2,) * c
-        out.append(tensors[len(idx)][idx])
+        acc = np.zeros_like(R[0])
+        for d in np.ndindex(*((3,) * len(idx))):
+            if not np.any(R[len(idx)][d]):
+                continue
+            term = R[len(idx)][d]
+            for ai, di in zip(idx, d):
+                term = term * L[ai, di]
+            acc = acc + term
+        out.append(acc)
     return np.array(out)
 
 
-def projections(n, ux, uy, T):
-    """a^(k) = int f_MJ J^(k) d^2p/p0, (16, ...)."""
-    C = polynomials()
-    M = mj_monomial_moments(n, ux, uy, T)
-    return np.einsum("kb,b...->k...", C, M)
-
-
-def equilibrium(n, ux, uy, T):
-    """f^eq_i (45, ...) (Eq. feq-expansion-discrete)."""
+@lru_cache(maxsize=None)
+def _rest_projection_and_nodes():
+    """a^(k) at rest (n = T = 1, u = 0) and the table J^(k)(p_i) (16, 45), both
+    from the 60-digit Gram-Schmidt, rounded to FP64.  At rest f_MJ = omega / (m + 1)."""
+    n = len(MONOMIALS)
+    G = [[omega_moment(a1 + a2, b1 + b2, c1 + c2) for (a2, b2, c2) in MONOMIALS]
+         for (a1, b1, c1) in MONOMIALS]
     q = quadrature()
+    with decimal.localcontext(_ctx()):
+        D = decimal.Decimal
+        C = _gram_schmidt_decimal(G)
+        Mr = [D(omega_moment(*mon).numerator) / D(omega_moment(*mon).denominator) / D(MASS + 1)
+              for mon in MONOMIALS]
+        a_rest = np.array([float(sum(C[k][b] * Mr[b] for b in range(n))) for k in range(n)])
+        v0 = D(q["v0"])
+        J = np.zeros((n, Q))
+        for i in range(Q):
+            k = q["cls"][i]
+            n2 = int(q["n"][i, 0]) ** 2 + int(q["n"][i, 1]) ** 2
+            p0 = D(MASS) / (D(1) - v0 * v0 * n2).sqrt()
+            p = (p0, p0 * v0 * int(q["n"][i, 0]), p0 * v0 * int(q["n"][i, 1]))
+            mv = [_pw(p[0], a) * _pw(p[1], b) * _pw(p[2], c) for (a, b, c) in MONOMIALS]
+            for kk in range(n):
+                J[kk, i] = float(sum(C[kk][b] * mv[b] for b in range(n)))
+    return a_rest, J
+
+
+def projections(n, ux, uy, T):
+    """a^(k) = int f_MJ J^(k) d^2p/p0, (16, ...): the rest value (exact) plus
+    C times the moments' deviation from rest, taken in longdouble before the
+    FP64 product (so the large entries of C never multiply rounded O(1)
+    moments)."""
     C = polynomials()
-    a = projections(n, ux, uy, T)
-    J = C @ monomial_values(q["p"].T)                 # (16, 45): J^(k)(p_i)
+    a_rest, _ = _rest_projection_and_nodes()
+    nd = np.ndim(n)
+    dM = (mj_monomial_moments(n, ux, uy, T) - _rest_moments().reshape((-1,) + (1,) * nd)).astype(float)
+    return a_rest.reshape((-1,) + (1,) * nd) + np.einsum("kb,b...->k...", C, dM)
+
+
+@lru_cache(maxsize=None)
+def _rest_moments():
+    one = np.ones(1)
+    return mj_monomial_moments(one, 0 * one, 0 * one, one)[:, 0]
+
+
+def equilibrium(n, ux, uy, T, a=None):
+    """f^eq_i (45, ...) (Eq. feq-expansion-discrete); `a` may pass the
+    projections already computed for these fields."""
+    q = quadrature()
+    if a is None:
+        a = projections(n, ux, uy, T)
+    _, J = _rest_projection_and_nodes()               # (16, 45): J^(k)(p_i)
     return q["w"].reshape((Q,) + (1,) * np.ndim(n)) * np.einsum("ki,k...->i...", J, a)
 
 
@@ -430,11 +485,13 @@ def macroscopic(f):
     return landau(*moments(f))
 
 
-def force_term(n, ux, uy, T, Fx, Fy):
+def force_term(n, ux, uy, T, Fx, Fy, a=None):
     """F_i^ext = w_i [ (F.v_i) P(p_i) - F.grad_p P(p_i) ], (45, ...)."""
     q = quadrature()
     C = polynomials()
-    coef = np.einsum("kb,k...->b...", C, projections(n, ux, uy, T))   # P in MONOMIALS
+    if a is None:
+        a = projections(n, ux, uy, T)
+    coef = np.einsum("kb,k...->b...", C, a)           # P in MONOMIALS
     p = q["p"].T
     v = p[1:] / p[0]
     d0 = np.zeros((len(MONOMIALS), Q))
@@ -462,13 +519,14 @@ def collide(f, tau, Fx=0.0, Fy=0.0):
     """f* = f - (p.U / (p0 tau)) (f - f^eq) + F^ext (Eq. discrete-rbe)."""
     q = quadrature()
     n, ux, uy, T = macroscopic(f)
-    feq = equilibrium(n, ux, uy, T)
+    a = projections(n, ux, uy, T)
+    feq = equilibrium(n, ux, uy, T, a)
     g = 1.0 / np.sqrt(1.0 - ux * ux - uy * uy)
     v = q["p"][:, 1:] / q["p"][:, :1]
     om = g * (1.0 - np.einsum("i,...->i...", v[:, 0], ux) - np.einsum("i,...->i...", v[:, 1], uy)) / tau
     out = f - om * (f - feq)
     if Fx != 0.0 or Fy != 0.0:
-        out = out + force_term(n, ux, uy, T, Fx, Fy)
+        out = out + force_term(n, ux, uy, T, Fx, Fy, a)
     return out
 
 
