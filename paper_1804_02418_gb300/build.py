@@ -24,7 +24,7 @@ LIB = os.path.join(LIBDIR, "librlbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "quadrature.cpp", "kernels_f64.cu", "kernels_f32.cu",
            "kernels_f16.cu", "kernels_bf16.cu", "residual_static.cu",
-           "fno_kernels.cu"]
+           "fno_kernels.cu", "massive_quadrature.cpp", "massive.cu"]
 
 
 def nvcc() -> str:
@@ -46,7 +46,7 @@ def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, src + ".o")
     srcp = os.path.join(CSRC, src)
     deps = [srcp] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
-    deps.append(os.path.join(INCLUDE, "rlbm.h"))
+    deps += [os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE) if h.endswith(".h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc(), "-c", srcp, "-o", obj] + _flags(src)

@@ -1,0 +1,170 @@
+"""Massive-particle variant (m = 5 T0, Sec. 2.3, Fig. m5-stencil) on the GPU
+against the oracle (oracle/massive.py), through the C ABI of
+include/rlbm_massive.h.
+
+* Parity after 100 steps, normwise in n, u, T (the bars of the massless
+  path): FP64 1e-12, FP32 1e-5; periodic box, channel with a force, closed
+  box with a force (bounce-back on both axes), sizes spanning several
+  32 x 4 blocks with ragged edges.
+* The initial state equals the oracle's f^eq element by element; state
+  I/O round trips (FP32 exactly, FP64 within one ulp).
+* At the bench size (1024 x 512 channel), two steps from random fields
+  agree with the oracle at every site.
+* The rest state stays at rest; a shear wave decays at the Chapman-Enskog
+  rate of the discrete model (0.15 % at 128 sites, as the oracle does).
+* Unphysical initial fields are rejected; the error word reports none for
+  valid runs.
+"""
+import numpy as np
+import pytest
+
+from oracle import massive as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_02418_gb300 import build, massive
+    build.build()
+    return massive
+
+
+def random_fields(nx, ny, seed, du=0.02, dn=0.005, dT=0.005):
+    rng = np.random.default_rng(seed)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    # smooth large-scale flow plus site noise
+    ux = du * (np.sin(2 * np.pi * y / ny) + 0.3 * rng.standard_normal((ny, nx)))
+    uy = du * (np.cos(2 * np.pi * x / nx) + 0.3 * rng.standard_normal((ny, nx)))
+    n = 1 + dn * rng.standard_normal((ny, nx))
+    T = 1 + dT * rng.standard_normal((ny, nx))
+    return [np.ascontiguousarray(a) for a in (n, ux, uy, T)]
+
+
+def normwise(got, ref):
+    n, ux, uy, T = got
+    rn, rux, ruy, rT = ref
+    du = np.sqrt((ux - rux) ** 2 + (uy - ruy) ** 2).max() / np.sqrt(rux ** 2 + ruy ** 2).max()
+    return max(np.abs(n - rn).max() / np.abs(rn).max(), du, np.abs(T - rT).max() / np.abs(rT).max())
+
+
+CASES = {
+    "periodic": dict(nx=70, ny=45, periodic_x=True, periodic_y=True, tau=0.9),
+    "channel_force": dict(nx=64, ny=37, periodic_x=True, periodic_y=False, tau=0.8, Fx=2e-5),
+    "box_force": dict(nx=41, ny=38, periodic_x=False, periodic_y=False, tau=1.1, Fx=1e-5, Fy=-2e-5),
+}
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    out = {}
+    for name, c in CASES.items():
+        lat = M.Lattice(c["nx"], c["ny"], c["periodic_x"], c["periodic_y"], c["tau"],
+                        c.get("Fx", 0.0), c.get("Fy", 0.0))
+        f = random_fields(c["nx"], c["ny"], 7)
+        post = M.run(lat, M.init(lat, *f), 100)
+        out[name] = (f, M.fields(lat, post))
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("case", list(CASES))
+def test_parity_with_the_oracle(ms, oracle_runs, prec, tol, case):
+    c = CASES[case]
+    f, ref = oracle_runs[case]
+    with ms.MassiveSolver(prec=prec, **c) as sv:
+        sv.init(*f)
+        sv.step(100)
+        got = sv.moments()
+        sv.check()
+    err = normwise(got, ref)
+    print(f"{case} {prec}: normwise {err:.3e}")
+    assert err <= tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_initial_state_is_the_oracle_equilibrium(ms, prec):
+    nx, ny = 37, 21
+    f = random_fields(nx, ny, 3, du=0.1, dn=0.05, dT=0.05)
+    ref = M.equilibrium(*f) - M.rest_populations()[:, None, None]
+    with ms.MassiveSolver(nx, ny, True, True, prec=prec) as sv:
+        sv.init(*f)
+        got = sv.get_state()
+        scale = np.abs(ref).max(axis=(1, 2), keepdims=True)
+        err = (np.abs(got - ref) / scale).max()
+        print(f"{prec}: max |delta - oracle| / scale per population {err:.3e}")
+        assert err < (1e-12 if prec == "f64" else 2e-6)
+        # state I/O round trip
+        sv.set_state(got)
+        back = sv.get_state()
+        if prec == "f32":
+            assert np.array_equal(back, got)
+        else:
+            assert np.allclose(back, got, rtol=2.3e-16, atol=0)
+
+
+def test_bench_size_two_steps_agree_everywhere(ms):
+    nx, ny = 1024, 512
+    f = random_fields(nx, ny, 11, du=0.01, dn=0.002, dT=0.002)
+    lat = M.Lattice(nx, ny, True, False, 1.0, 1e-6, 0.0)
+    ref = M.fields(lat, M.run(lat, M.init(lat, *f), 2))
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-5)):
+        with ms.MassiveSolver(nx, ny, True, False, 1.0, 1e-6, 0.0, prec=prec) as sv:
+            sv.init(*f)
+            sv.step(2)
+            got = sv.moments()
+            sv.check()
+        err = normwise(got, ref)
+        print(f"1024 x 512 {prec}: normwise {err:.3e}")
+        assert err <= tol
+
+
+def test_rest_state_stays_at_rest(ms):
+    with ms.MassiveSolver(40, 30, False, False, 0.7, prec="f64") as sv:
+        sv.init()
+        sv.step(20)
+        n, ux, uy, T = sv.moments()
+        sv.check()
+    assert np.abs(n - 1).max() < 1e-14 and np.abs(T - 1).max() < 1e-14
+    assert np.abs(ux).max() < 1e-15 and np.abs(uy).max() < 1e-15
+
+
+def test_shear_wave_decays_at_the_chapman_enskog_rate(ms):
+    q = M.quadrature()
+    m, tau, ny, steps = M.MASS, 0.8, 128, 300
+    p, w = q["p"], q["w"]
+    eta_d = (tau - 0.5) / (m + 1) * np.sum(w * (p[:, 1] * p[:, 2]) ** 2 / p[:, 0])
+    h = (m * m + 3 * m + 3) / (m + 1)
+    k = 2 * np.pi / (ny * q["v0"])
+    pred = eta_d / h * k * k
+    y = np.arange(ny)[:, None] * np.ones((1, 8))
+    basis = np.sin(2 * np.pi * y / ny)
+    o = np.ones_like(basis)
+    amps = []
+    with ms.MassiveSolver(8, ny, True, True, tau, prec="f32") as sv:
+        sv.init(o, np.ascontiguousarray(1e-3 * basis), 0 * o, o)
+        for _ in range(steps):
+            sv.step(1)
+            ux = sv.moments()[1]
+            amps.append((ux * basis).sum() / (basis * basis).sum())
+        sv.check()
+    t = np.arange(1, steps + 1)
+    rate = -np.polyfit(t[steps // 4:], np.log(np.abs(amps))[steps // 4:], 1)[0]
+    print(f"shear rate {rate:.6e} vs Chapman-Enskog {pred:.6e}: {rate / pred - 1:+.2e}")
+    assert abs(rate / pred - 1) < 1.5e-3
+
+
+def test_unphysical_initial_fields_are_rejected(ms):
+    nx, ny = 16, 12
+    o = np.ones((ny, nx))
+    bad = o.copy()
+    bad[3, 4] = 1.2                       # |u| > 1 at one site
+    with ms.MassiveSolver(nx, ny, True, True, prec="f32") as sv:
+        with pytest.raises(Exception):
+            sv.init(o, bad, 0 * o, o)
+        sv.init(o, 0 * o, 0 * o, o)       # the context stays usable
+        sv.step(3)
+        sv.check()

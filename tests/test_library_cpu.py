@@ -4,7 +4,9 @@
   include/rlbm.h;
 * the host-only quadrature refinement agrees with the oracle's (stored in
   tests/golden/quadrature_refined.txt by tests/golden/make_golden.py);
-* argument validation (rlbm_workspace_size touches no device).
+* argument validation (rlbm_workspace_size touches no device);
+* the massive-particle quadrature (host-only solve, Sec. 2.3) equals the
+  oracle's: the same v0, interval and weights.
 """
 import ctypes
 import os
@@ -13,7 +15,7 @@ import re
 import numpy as np
 import pytest
 
-from paper_1804_02418_gb300 import fno, rlbm, workloads  # fno registers its exports
+from paper_1804_02418_gb300 import fno, massive, rlbm, workloads  # fno, massive register their exports
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -113,3 +115,27 @@ def test_bad_precision_and_empty_config(lib):
     cfg.nsamples = 0
     n = ctypes.c_size_t()
     assert lib.rlbm_workspace_size(ctypes.byref(cfg), ctypes.byref(n)) == -1
+
+
+def test_massive_quadrature_matches_the_oracle(lib):
+    from oracle import massive as M
+    q = M.quadrature()
+    got = massive.quadrature()
+    assert got["v0"] == q["v0"]
+    assert np.allclose(got["window"], q["window"], rtol=1e-15, atol=0)
+    assert np.allclose(got["w"], q["w_class"], rtol=1e-13, atol=0)
+    assert np.allclose(got["p0"], q["p0_class"], rtol=1e-15, atol=0)
+    assert np.array_equal(massive.stencil(), q["n"])
+
+
+@pytest.mark.parametrize("bad", [dict(nx=4), dict(ny=200000), dict(tau=0.5), dict(Fx=0.02),
+                                 dict(prec=2)])
+def test_massive_invalid_configs_are_rejected(lib, bad):
+    cfg = massive._Config()
+    cfg.nx, cfg.ny, cfg.tau, cfg.prec = 32, 16, 1.0, 1
+    for k, v in bad.items():
+        setattr(cfg, k, v)
+    ctx = ctypes.c_void_p()
+    assert lib.rlbm_massive_create(ctypes.byref(cfg), ctypes.byref(ctx)) == -1
+    assert not ctx.value
+    assert lib.rlbm_massive_last_error(None)
