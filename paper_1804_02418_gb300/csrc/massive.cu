@@ -151,6 +151,30 @@ __device__ __forceinline__ void mpull(const S* __restrict__ src, const MGeom& g,
   f[kRestPop] = __ldg(src + (long long)kRestPop * g.plane + site);
 }
 
+// The same for a block lying at least kReach sites inside every edge: no
+// wrap, no bounce-back; each offset is uniform across the block.
+template <typename S>
+__device__ __forceinline__ void mpull_interior(const S* __restrict__ src, const MGeom& g,
+                                               long long site, S (&f)[kQm]) {
+  const S* base = src + site;
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * p + h;
+      const int ex = h ? -pair_x(p) : pair_x(p);
+      const int ey = h ? -pair_y(p) : pair_y(p);
+      f[i] = __ldg(base + ((long long)i * g.plane - (long long)ey * g.ldx - ex));
+    }
+  }
+  f[kRestPop] = __ldg(base + (long long)kRestPop * g.plane);
+}
+
+__device__ __forceinline__ bool block_interior(const MGeom& g) {
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 4;
+  return x0 >= kReach && x0 + 31 < g.nx - kReach && y0 >= kReach && y0 + 3 < g.ny - kReach;
+}
+
 template <typename R>
 __device__ __forceinline__ MMom<R> mmoments(const R (&g)[kQm]) {
   const MConsts<R>& c = mc<R>();
@@ -460,7 +484,8 @@ __global__ void __launch_bounds__(128) k_mstep(const R* __restrict__ src, R* __r
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y;
   if (x >= geo.nx || y >= geo.ny) return;
   R g[kQm];
-  mpull(src, geo, x, y, g);
+  if (block_interior(geo)) mpull_interior(src, geo, (long long)y * geo.ldx + x, g);
+  else mpull(src, geo, x, y, g);
   const MMom<R> mo = mmoments(g);
   MMacro<R> M;
   const bool conv = mlandau(mo, M);
