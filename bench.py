@@ -2,6 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f32|f64|f16dev|bf16dev]
                     [--impl ours|reference] [--no-cpu-baseline]
+                    [--workload graphene|ensemble|massive]
 
 Workload: the graphene-like sample, 1024 x 512 sites, no-slip walls, injector
 and collector contacts 32 sites wide on the y = 0 edge with centres 256 apart,
@@ -55,10 +56,13 @@ def parse():
     ap.add_argument("--tune-cache", default=None,
                     help="file where the launch-shape autotuner keeps its choice (a later run "
                          "with the same file reuses it instead of timing the candidates)")
-    ap.add_argument("--workload", default="graphene", choices=["graphene", "ensemble"],
+    ap.add_argument("--workload", default="graphene", choices=["graphene", "ensemble", "massive"],
                     help="graphene: the 1024x512 sample (default line); ensemble: the "
-                         "256-sample uneven ensemble, sharded by sample over the ranks")
+                         "256-sample uneven ensemble, sharded by sample over the ranks; "
+                         "massive: the m = 5 T0 variant on its 45-vector stencil, 1024x512 channel")
     ap.add_argument("--ensemble-size", type=int, default=256)
+    ap.add_argument("--force", type=float, default=1e-6,
+                    help="massive workload: the uniform force along x (0: none)")
     return ap.parse_args()
 
 
@@ -71,25 +75,38 @@ def peaks():
     return FALLBACK_HBM, "fallback"
 
 
-def source_hash():
+# the sources each profiled step kernel is compiled from
+KERNEL_SOURCES = {
+    "f64": ["kernels.cuh", "site.cuh", "prec_impl.cuh", "ops.h", "kernels_f64.cu"],
+    "f32": ["kernels.cuh", "site.cuh", "prec_impl.cuh", "ops.h", "kernels_f32.cu"],
+    "f16dev": ["kernels.cuh", "site.cuh", "prec_impl.cuh", "ops.h", "kernels_f16.cu"],
+    "bf16dev": ["kernels.cuh", "site.cuh", "prec_impl.cuh", "ops.h", "kernels_bf16.cu"],
+    "massive_f32": ["massive.cu", "massive_tables.h", "massive_quadrature.cpp", "dd.h"],
+    "massive_f64": ["massive.cu", "massive_tables.h", "massive_quadrature.cpp", "dd.h"],
+}
+
+
+def source_hash(key="f32"):
+    """Hash of the sources the step kernel of `key` is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1804_02418_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in sorted(KERNEL_SOURCES[key]):
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(prec):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when the kernel sources changed since it was taken."""
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (key: the precision, or "massive_<precision>"), or None when the kernel
+    sources changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(prec)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or prec not in KERNEL_SOURCES or e.get("source_hash") != source_hash(prec):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -175,7 +192,88 @@ def cpu_baseline(steps):
                       f"{len(d['times'])} steps in {t1:.1f} s"}
 
 
+MASSIVE_WORKLOAD = ("massive-particle fluid m = 5 T0 (45-vector stencil), channel 1024x512, "
+                    "periodic along x, walls at y = 0 and y = ny - 1, F = 1e-6 along x, tau = 1, "
+                    "from rest")
+
+MASSIVE_ORACLE_SNIPPET = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from oracle import massive as M
+nx, ny, steps, warm = {nx}, {ny}, {steps}, {warm}
+M.quadrature(); M.polynomials(); M._rest_projection_and_nodes()
+lat = M.Lattice(nx, ny, True, False, 1.0, 1e-6, 0.0)
+o = np.ones((ny, nx))
+post = M.init(lat, o, 0 * o, 0 * o, o)
+for _ in range(warm):
+    post = M.step(lat, post)
+times = []
+for _ in range(steps):
+    t0 = time.perf_counter()
+    post = M.step(lat, post)
+    times.append(time.perf_counter() - t0)
+print(json.dumps(dict(sites=nx * ny, times=times)))
+"""
+
+
+def run_massive_oracle(nx, ny, steps, warm, copies=1):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    code = MASSIVE_ORACLE_SNIPPET.format(root=ROOT, nx=nx, ny=ny, steps=steps, warm=warm)
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for _ in range(copies)]
+    out = []
+    for p in procs:
+        o, e = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(e[-2000:])
+        out.append(json.loads(o.strip().splitlines()[-1]))
+    return out
+
+
+def massive_cpu_baseline(steps, nx=256, ny=128):
+    """The massive-particle oracle on a bounded sample of the same geometry
+    (256x128; one copy per host core, memory permitting, and one copy alone)."""
+    one = run_massive_oracle(nx, ny, steps, 1)[0]
+    t1 = sum(one["times"])
+    copies = host_copies()
+    runs = run_massive_oracle(nx, ny, max(2, steps // 2), 1, copies)
+    tm = max(sum(r["times"]) for r in runs)
+    many = copies * one["sites"] * len(runs[0]["times"]) / tm / 1e9
+    return {"value": many, "unit": "GLUPS", "cores": copies, "kind": "oracle",
+            "value_1core": one["sites"] * len(one["times"]) / t1 / 1e9,
+            "sample": f"{copies} concurrent single-threaded copies x {len(runs[0]['times'])} steps "
+                      f"of the same channel scaled to {nx}x{ny} (FP64 numpy, extended-precision "
+                      f"moments; slowest copy {tm:.1f} s); 1 core alone: {len(one['times'])} steps "
+                      f"in {t1:.1f} s"}
+
+
+def massive_reference_arm(args):
+    copies = host_copies()
+    nx, ny = 128, 64
+    runs = run_massive_oracle(nx, ny, args.steps, args.warmup, copies)
+    t = max(sum(r["times"]) for r in runs)
+    value = copies * runs[0]["sites"] * args.steps / t / 1e9
+    sample = (f"{copies} concurrent single-threaded copies x {args.steps} oracle steps of the "
+              f"same channel scaled to {nx}x{ny} (bounded so the run ends within minutes), FP64 numpy")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": MASSIVE_WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": copies, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def reference_arm(args):
+    if args.workload == "massive":
+        return massive_reference_arm(args)
     ladder = [(1024, 512), (512, 256), (256, 128), (128, 64), (64, 32), (32, 16)]
     budget = 150.0
     chosen = ladder[-1]
@@ -378,6 +476,113 @@ def gpu_arm(args, rank, world, cpu_line):
     print(json.dumps(line), flush=True)
 
 
+def massive_arm(args, rank, world, cpu_line):
+    """The massive-particle variant (m = 5 T0) on the 1024x512 channel: same
+    timing rules as the default line (L2 flushed before every timed step,
+    steps timed alone; e2e through the C ABI with pinned host fields)."""
+    import numpy as np
+    import torch
+
+    from paper_1804_02418_gb300 import build, massive, parallel
+
+    if args.prec not in ("f32", "f64"):
+        raise SystemExit("the massive variant stores f32 or f64")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    nx, ny = 1024, 512
+    sites = nx * ny
+    stream = torch.cuda.Stream()
+    sv = massive.MassiveSolver(nx, ny, True, False, 1.0, args.force, 0.0, prec=args.prec, stream=stream)
+    flush = torch.empty(max(2 * L2_BYTES, 256 << 20), dtype=torch.uint8, device="cuda")
+    evict = torch.ones(max(2 * L2_BYTES, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    sink = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        flush.zero_()
+        torch.sum(evict, dim=0, out=sink)
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        sv.init()
+        for _ in range(args.warmup):
+            flush_l2()
+            sv.step(1)
+    sync_all()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = sv.launches
+    sync_all()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush_l2()
+            ev[k][0].record(stream)
+            sv.step(1)
+            ev[k][1].record(stream)
+    sync_all()
+    launches = sv.launches - l0
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    sv.check()
+    t_ms = parallel.max_over_ranks(t_ms, device="cuda")
+
+    host_in = [torch.ones((ny, nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    host_in[1].zero_()
+    host_in[2].zero_()
+    host_out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    sync_all()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sv.init(*[h.numpy() for h in host_in])
+    sv.step(args.steps)
+    sv.moments(out=[h.numpy() for h in host_out])
+    e1.record(stream)
+    sync_all()
+    e2e_ms = parallel.max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    finite = bool(np.isfinite(host_out[1].numpy()).all())
+    sv.check()
+    sv.close()
+    if rank != 0:
+        return
+    hbm, hbm_kind = peaks()
+    alg_bytes = 2 * 45 * BYTES[args.prec] * sites
+    achieved = alg_bytes / (t_ms / 1e3 / args.steps) / 1e9
+    field_bytes = 4 * 8 * sites
+    line = {
+        "metric": METRIC, "value": world * sites * args.steps / (t_ms / 1e3) / 1e9, "unit": "GLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": MASSIVE_WORKLOAD if args.force == 1e-6 else
+                   MASSIVE_WORKLOAD.replace("F = 1e-6", f"F = {args.force:g}"),
+                   "precision": args.prec, "sites": sites,
+                   "l2": "before every timed step a 2x L2 buffer is written, then another 2x L2 "
+                         "buffer read (cold L2, no pending write-backs); steps timed alone",
+                   "parallelism": "replicas only" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": ncu_traffic("massive_" + args.prec),
+                     "peak_kind": hbm_kind, "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": {"value": world * sites * args.steps / (e2e_ms / 1e3) / 1e9, "unit": "GLUPS",
+                "h2d_bytes_per_step": field_bytes / args.steps,
+                "d2h_bytes_per_step": field_bytes / args.steps},
+        "gpu_launches": launches, "clocks": clk, "fields_finite": finite,
+    }
+    if cpu_line is not None:
+        line["cpu_baseline"] = cpu_line
+    print(json.dumps(line), flush=True)
+
+
 def ensemble_arm(args, rank, world):
     """The uneven ensemble, sharded by sample over the ranks (no data-path
     collective).  Its working set is far larger than L2, so steps run back to
@@ -481,6 +686,8 @@ def main():
     cpu_line = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "graphene":
         cpu_line = cpu_baseline(args.cpu_sample_steps)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "massive":
+        cpu_line = massive_cpu_baseline(args.cpu_sample_steps)
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -489,6 +696,8 @@ def main():
     try:
         if args.workload == "ensemble":
             ensemble_arm(args, rank, world)
+        elif args.workload == "massive":
+            massive_arm(args, rank, world, cpu_line)
         else:
             gpu_arm(args, rank, world, cpu_line)
     finally:

@@ -321,22 +321,39 @@ __device__ __forceinline__ EqSite<R> eq_site(const MMacro<R>& M) {
   return e;
 }
 
+// Parities in (ux, uy) / (px, py) of the table columns: a node on an axis
+// is its own mirror image across that axis, so every entry odd in the other
+// component vanishes there.  WE: dn dT, dT^2, ux^2, ux uy, uy^2; WO: dn ux,
+// dn uy, dT ux, dT uy; BE / BO: the E / O monomials.
+__host__ __device__ constexpr bool we_odd(int k) { return k == 3; }                 // in x and in y
+__host__ __device__ constexpr bool wo_x(int k) { return k == 0 || k == 2; }         // odd in x only
+__host__ __device__ constexpr bool be_odd(int k) { return k == 3 || k == 6; }       // in x and in y
+__host__ __device__ constexpr bool bo_x(int k) { return k == 0 || k == 2 || k == 4 || k == 6; }
+// whether a column with the given parities can be nonzero at pair p
+__host__ __device__ constexpr bool live(int p, bool odd_x, bool odd_y) {
+  return !((odd_x && pair_x(p) == 0) || (odd_y && pair_y(p) == 0));
+}
+
 // even and odd parts of g^eq for pair p (g^eq of 2p = even + odd, of 2p+1 = even - odd)
 template <typename R>
 __device__ __forceinline__ void eq_pair(const EqSite<R>& e, int p, R& even, R& odd) {
   const MConsts<R>& c = mc<R>();
   R ev = fma(c.LT[p], e.dT, e.dn);
 #pragma unroll
-  for (int k = 0; k < 5; ++k) ev = fma(c.WE[p][k], e.qE[k], ev);
+  for (int k = 0; k < 5; ++k)
+    if (live(p, we_odd(k), we_odd(k))) ev = fma(c.WE[p][k], e.qE[k], ev);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) ev = fma(c.BE[p][k], e.E[k], ev);
+  for (int k = 0; k < 8; ++k)
+    if (live(p, be_odd(k), be_odd(k))) ev = fma(c.BE[p][k], e.E[k], ev);
   R od = R(0);
   if (pair_x(p) != 0) od = fma(c.LX[p], e.ux, od);
   if (pair_y(p) != 0) od = fma(c.LY[p], e.uy, od);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) od = fma(c.WO[p][k], e.qO[k], od);
+  for (int k = 0; k < 4; ++k)
+    if (live(p, wo_x(k), !wo_x(k))) od = fma(c.WO[p][k], e.qO[k], od);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) od = fma(c.BO[p][k], e.O[k], od);
+  for (int k = 0; k < 8; ++k)
+    if (live(p, bo_x(k), !bo_x(k))) od = fma(c.BO[p][k], e.O[k], od);
   even = ev;
   odd = od;
 }
@@ -346,9 +363,11 @@ __device__ __forceinline__ R eq_rest(const EqSite<R>& e) {
   const MConsts<R>& c = mc<R>();
   R ev = fma(c.restLT, e.dT, e.dn);
 #pragma unroll
-  for (int k = 0; k < 5; ++k) ev = fma(c.restWE[k], e.qE[k], ev);
+  for (int k = 0; k < 5; ++k)
+    if (!we_odd(k)) ev = fma(c.restWE[k], e.qE[k], ev);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) ev = fma(c.restBE[k], e.E[k], ev);
+  for (int k = 0; k < 8; ++k)
+    if (!be_odd(k)) ev = fma(c.restBE[k], e.E[k], ev);
   return ev;
 }
 
