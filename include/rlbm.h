@@ -116,8 +116,8 @@ typedef struct {
   int graph_steps;              /* > 0 (even): rlbm_step replays CUDA graphs of this many
                                    steps, captured on first use; needs a non-NULL
                                    stream.  0: plain launches */
-  const char* tune_cache;       /* optional file where rlbm_autotune keeps its choices
-                                   (one line per GPU / precision / workload), or NULL */
+  const char* tune_cache;       /* optional JSON file where rlbm_autotune keeps its choices
+                                   (one entry per GPU / precision / workload), or NULL */
 } rlbm_config;
 
 typedef struct rlbm_ctx rlbm_ctx;
@@ -156,8 +156,9 @@ int rlbm_sample_residuals(const rlbm_ctx* ctx, double* out);
  * 1..16 per SM, persistent) and whether the pulls are staged in shared memory
  * (0 none; 1 bulk asynchronous copies of the 12 shifted row segments of a
  * tile, the next tile in flight while the current one is computed).  With
- * rlbm_config.tune_cache the choice is read from / appended to that file
- * (one line "key bx grid staged").  Needs an initialised state.  Writes the
+ * rlbm_config.tune_cache the choice is read from / added to that file
+ * (a JSON object {"<key>": {"bx": B, "grid": G, "staged": S}, ...}, the key
+ * naming the GPU, the precision and the batch's geometry).  Needs an initialised state.  Writes the
  * choice to *bx, *grid and *staged (each may be NULL).  The staged kernels
  * bound every wait (about 1 s); a wait that gives up raises the error bit
  * that rlbm_check reports as RLBM_ETIMEOUT. */

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -695,26 +696,87 @@ int rlbm_set_launch_shape(rlbm_ctx* c, int bx, int grid, int staged) {
   return RLBM_OK;
 }
 
+namespace {
+
+// The autotuner's cache file: one JSON object,
+//   {"<key>": {"bx": B, "grid": G, "staged": S}, ...}
+// (keys from tune_key: GPU name, precision, batch and geometry hash).
+struct TuneEntry {
+  std::string key;
+  int bx, grid, staged;
+};
+
+bool json_int(const std::string& s, size_t from, size_t to, const char* name, int* v) {
+  const std::string pat = std::string("\"") + name + "\"";
+  size_t k = s.find(pat, from);
+  if (k == std::string::npos || k >= to) return false;
+  k = s.find(':', k + pat.size());
+  if (k == std::string::npos || k >= to) return false;
+  char* end = nullptr;
+  const long x = std::strtol(s.c_str() + k + 1, &end, 10);
+  if (end == s.c_str() + k + 1) return false;
+  *v = (int)x;
+  return true;
+}
+
+std::vector<TuneEntry> read_tune_cache(const std::string& path) {
+  std::vector<TuneEntry> out;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return out;
+  std::string s;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, n);
+  fclose(f);
+  size_t pos = s.find('{');
+  if (pos == std::string::npos) return out;
+  ++pos;
+  while (true) {
+    const size_t q0 = s.find('"', pos);
+    if (q0 == std::string::npos) break;
+    const size_t q1 = s.find('"', q0 + 1);
+    if (q1 == std::string::npos) break;
+    const size_t b0 = s.find('{', q1);
+    if (b0 == std::string::npos) break;
+    const size_t b1 = s.find('}', b0);
+    if (b1 == std::string::npos) break;
+    TuneEntry e{s.substr(q0 + 1, q1 - q0 - 1), 0, 0, 0};
+    if (json_int(s, b0, b1, "bx", &e.bx) && json_int(s, b0, b1, "grid", &e.grid) &&
+        json_int(s, b0, b1, "staged", &e.staged))
+      out.push_back(e);
+    pos = b1 + 1;
+  }
+  return out;
+}
+
+void write_tune_cache(const std::string& path, const std::vector<TuneEntry>& entries) {
+  const std::string tmp = path + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "{\n");
+  for (size_t i = 0; i < entries.size(); ++i)
+    fprintf(f, "  \"%s\": {\"bx\": %d, \"grid\": %d, \"staged\": %d}%s\n", entries[i].key.c_str(),
+            entries[i].bx, entries[i].grid, entries[i].staged, i + 1 < entries.size() ? "," : "");
+  fprintf(f, "}\n");
+  fclose(f);
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+}  // namespace
+
 int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out, int* staged_out) {
   if (!c) return RLBM_EINVAL;
   if (!c->initialised) return fail(c, RLBM_ESTATE, "rlbm_init or rlbm_set_state first");
   const std::string key = tune_key(c);
   bool found = false;
   if (!c->tune_cache.empty()) {
-    if (FILE* f = fopen(c->tune_cache.c_str(), "r")) {
-      char line[768];
-      while (fgets(line, sizeof line, f)) {
-        char k[640];
-        int bx, grid, staged = 0;
-        const int got = sscanf(line, "%639s %d %d %d", k, &bx, &grid, &staged);
-        if (got >= 3 && key == k && valid_shape(bx, grid, staged)) {
-          c->bx = bx;
-          c->grid = grid;
-          c->staged = staged;
-          found = true;
-        }
+    for (const TuneEntry& e : read_tune_cache(c->tune_cache)) {
+      if (e.key == key && valid_shape(e.bx, e.grid, e.staged)) {
+        c->bx = e.bx;
+        c->grid = e.grid;
+        c->staged = e.staged;
+        found = true;
       }
-      fclose(f);
     }
   }
   if (!found) {
@@ -767,10 +829,12 @@ int rlbm_autotune(rlbm_ctx* c, int* bx_out, int* grid_out, int* staged_out) {
     c->grid = pick.grid;
     c->staged = pick.staged;
     if (!c->tune_cache.empty()) {
-      if (FILE* f = fopen(c->tune_cache.c_str(), "a")) {
-        fprintf(f, "%s %d %d %d\n", key.c_str(), c->bx, c->grid, c->staged);
-        fclose(f);
-      }
+      std::vector<TuneEntry> entries = read_tune_cache(c->tune_cache);
+      bool replaced = false;
+      for (TuneEntry& e : entries)
+        if (e.key == key) { e.bx = c->bx; e.grid = c->grid; e.staged = c->staged; replaced = true; }
+      if (!replaced) entries.push_back({key, c->bx, c->grid, c->staged});
+      write_tune_cache(c->tune_cache, entries);
     }
   }
   drop_graphs(c);

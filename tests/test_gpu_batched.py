@@ -188,15 +188,23 @@ def test_per_sample_residuals(rl, shape):
 
 def test_autotune_cache_round_trip(rl, tmp_path):
     samples = uneven_batch()[:3]
-    cache = str(tmp_path / "tune.txt")
+    import json
+    cache = str(tmp_path / "tune.json")
     with rl.Solver(samples, prec="f32", tune_cache=cache) as sv:
         for i, s in enumerate(samples):
             sv.init(i)
         first = sv.autotune()
-    lines = open(cache).read().splitlines()
-    assert len(lines) == 1 and lines[0].split()[1:] == [str(v) for v in first]
+    d = json.load(open(cache))
+    assert len(d) == 1
+    (entry,) = d.values()
+    assert (entry["bx"], entry["grid"], entry["staged"]) == tuple(first)
     with rl.Solver(samples, prec="f32", tune_cache=cache) as sv:
         for i, s in enumerate(samples):
             sv.init(i)
         assert sv.autotune() == first
-    assert len(open(cache).read().splitlines()) == 1
+    assert json.load(open(cache)) == d
+    # a second workload adds its own entry
+    with rl.Solver(samples[:1], prec="f32", tune_cache=cache) as sv:
+        sv.init(0)
+        sv.autotune()
+    assert len(json.load(open(cache))) == 2
