@@ -142,3 +142,32 @@ def test_viscosity_three_eighths_at_unit_tau():
     ratio = _decay_ratio(amps, 1.0, 64, 40, 300)
     eta = ratio * (1.0 - 0.5) / 4.0 * 3.0        # nu (eps + P), n = T = 1
     assert abs(eta - 3.0 / 8.0) < 0.01 * 3.0 / 8.0, eta
+
+
+def _strip_decay_ratio(ny, steps, tau=0.8, nx=16):
+    """Shear wave u_x = 0.01 sin(2 pi y / ny) on a doubly periodic strip (the
+    wave is uniform along x, so 16 columns suffice): decay rate over the
+    Chapman-Enskog rate nu k^2, nu = (tau - 1/2) c^2 / 4, c = 5 sites."""
+    s = W.Sample(nx, ny, periodic_x=True, periodic_y=True, tau=tau)
+    lat = lbm.Lattice(s)
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    basis = np.sin(2 * np.pi * y / ny)
+    o = np.ones_like(basis)
+    post = lbm.init(lat, o, 0.01 * basis, 0 * o, o)
+    amps = []
+    for _ in range(steps):
+        ux = lbm.macroscopic(lat, post)[1]
+        amps.append((ux * basis).sum() / (basis * basis).sum())
+        post = lbm.step(lat, post)
+    tt = np.arange(steps)
+    slope = np.polyfit(tt[steps // 10:], np.log(amps[steps // 10:]), 1)[0]
+    return -slope / ((tau - 0.5) * 25.0 / 4.0 * (2 * np.pi / ny) ** 2)
+
+
+def test_shear_decay_converges_at_second_order():
+    """Doubling the wavelength brings the decay rate about 4x closer to the
+    Chapman-Enskog value (lattice error ~ k^2)."""
+    e64 = abs(_strip_decay_ratio(64, 500) - 1)
+    e128 = abs(_strip_decay_ratio(128, 2000) - 1)
+    assert e64 < 0.01 and e128 < 0.0025
+    assert 3.0 < e64 / e128 < 5.0, (e64, e128)
