@@ -235,3 +235,56 @@ def test_zero_steps_is_a_no_op(rl):
         sv.step(0)
         b = sv.get_state()
     assert np.array_equal(a, b)
+
+
+def _window(s, fields, x0, y0, w=64):
+    """The w x w window of sample s at (x0, y0) as a sample of its own: the
+    window's edges that are edges of s keep their walls and contacts; its
+    other edges are artificial walls, more than 10 sites from every site
+    compared (one step and the moments' pull reach 10 sites)."""
+    contacts = []
+    for c in s.contacts:
+        # a contact on the lower edge, clipped to the window (its ghost values
+        # are the same along it)
+        lo, hi = max(c.x0, x0), min(c.x0 + c.length, x0 + w)
+        if c.edge == 0 and y0 == 0 and lo < hi:
+            contacts.append(W.Contact(0, lo - x0, hi - lo, u_n=c.u_n, n=c.n, T=c.T))
+    ws = W.Sample(w, w, tau=s.tau, Fx=s.Fx, Fy=s.Fy, contacts=contacts)
+    sub = [np.ascontiguousarray(f[y0:y0 + w, x0:x0 + w]) for f in fields]
+    ylo = 0 if y0 == 0 else 10
+    yhi = w if y0 + w == s.ny else w - 10
+    xlo = 0 if x0 == 0 else 10
+    xhi = w if x0 + w == s.nx else w - 10
+    return ws, sub, (slice(ylo, yhi), slice(xlo, xhi))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_4096x2048_sample_one_step_in_windows(rl, prec):
+    """The 4096 x 2048 graphene sample (walls, contacts 32 wide 256 apart,
+    F = 1e-6), random fields, one step in the autotuned launch shape; n, u, T
+    compared with the oracle run on 64 x 64 windows (interior, the lower
+    wall, both contacts, a corner) that contain every site those values
+    depend on."""
+    s = W.graphene_sample(nx=4096, ny=2048)
+    fields = [np.ascontiguousarray(f) for f in W.random_fields(s, 9, du=0.02, dn=0.01, dT=0.01)]
+    with rl.Solver(s, prec=prec) as sv:
+        sv.init(0, *fields)
+        sv.autotune()
+        sv.init(0, *fields)
+        sv.step(1)
+        got = sv.moments()
+        sv.check()
+    c0, c1 = s.contacts[0].x0, s.contacts[1].x0
+    windows = [(1000, 1000), (500, 0), (c0 - 16, 0), (c1 - 16, 0), (c0 + 10, 0),
+               (s.nx - 64, s.ny - 64), (0, 0)]
+    worst = {}
+    for x0, y0 in windows:
+        ws, sub, (ys, xs) = _window(s, fields, x0, y0)
+        lat = lbm.Lattice(ws)
+        ref = lbm.macroscopic(lat, lbm.run(lat, lbm.init(lat, *sub), 1))
+        g = [a[y0:y0 + 64, x0:x0 + 64][ys, xs] for a in got]
+        r = [a[ys, xs] for a in ref]
+        e = field_errors(g, r)
+        worst[(x0, y0)] = max(e.values())
+        assert max(e.values()) < TOL[prec], ((x0, y0), e)
+    print(f"4096 x 2048 {prec}: worst window error {max(worst.values()):.2e}")
