@@ -11,6 +11,11 @@
 3. Evaluation: held-out samples are converged from rest (cold) and from the
    operator's prediction (warm, f = f^eq of the predicted fields); steps and
    wall time to residual <= 1e-6 are compared.
+4. `--bound K`: on K held-out samples, the steps to residual <= 1e-6 from
+   seeds built out of the exact steady fields (as f^eq, partly, with the
+   first-order Chapman-Enskog non-equilibrium part), and the late decay rate
+   of the residual against the damping of the longest sound mode: what any
+   macroscopic seed could gain.
 
 Normalisation (from the linear Stokes response to a uniform force): with
 nu = 25 (tau - 1/2) / 4 sites^2 / step and the short side W, velocities are
@@ -106,18 +111,23 @@ def ctypes_stream(torch):
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=20, ref=None):
+def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=20, ref=None,
+             states=None, history=None):
     """Runs every sample to residual <= TOL; returns (steps per sample, wall seconds,
     final fields per sample, distances).  init: optional list of (n, ux, uy, T)
-    host arrays.  ref: optional reference steady fields; then `distances` holds,
-    per check and sample, ||u(t) - u_ref|| / ||u_ref|| (else None)."""
+    host arrays; states: optional list of stored states (f_i - w_i, [48][ny][nx])
+    set instead.  ref: optional reference steady fields; then `distances` holds,
+    per check and sample, ||u(t) - u_ref|| / ||u_ref|| (else None).  history:
+    optional list that receives the per-sample residuals of every check."""
     import torch
     stream = torch.cuda.Stream()
     dist = [] if ref is not None else None
     with torch.cuda.stream(stream):
         sv = rlbm.Solver(samples, prec=prec, stream=stream, graph_steps=graph_steps)
         for i in range(len(samples)):
-            if init is None:
+            if states is not None:
+                sv.set_state(np.ascontiguousarray(states[i], dtype=np.float64), i)
+            elif init is None:
                 sv.init(i)
             else:
                 sv.init(i, *[np.ascontiguousarray(a, dtype=np.float64) for a in init[i]])
@@ -130,6 +140,8 @@ def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=2
             sv.step(check, residual=True)
             steps += check
             r = sv.sample_residuals()
+            if history is not None:
+                history.append(r.copy())
             newly = (done < 0) & (r <= TOL)
             done[newly] = steps
             if ref is not None:
@@ -285,6 +297,95 @@ def evaluate(net, data, batch):
     return tot / max(cnt, 1)
 
 
+# ---------------------------------------------------------------------------
+# Residual analytics and the bound on what a macroscopic seed can gain
+# ---------------------------------------------------------------------------
+# direction hops of the 48-population stencil (population 4 d + j)
+HOPS = [(3, 4), (-3, -4), (-3, 4), (3, -4), (4, 3), (-4, -3), (-4, 3), (4, -3),
+        (5, 0), (-5, 0), (0, 5), (0, -5)]
+
+
+def decay_rates(history, check, lo=TOL, hi=100 * TOL):
+    """Late-time decay rate lambda (per step) of every sample's residual,
+    r(t) ~ C exp(-lambda t), fitted to the checks where lo <= r <= hi (NaN
+    when fewer than three)."""
+    h = np.array(history)                     # [checks, samples]
+    t = check * (np.arange(h.shape[0]) + 1)
+    out = np.full(h.shape[1], np.nan)
+    for i in range(h.shape[1]):
+        sel = (h[:, i] >= lo) & (h[:, i] <= hi)
+        if sel.sum() >= 3:
+            out[i] = -np.polyfit(t[sel], np.log(h[sel, i]), 1)[0]
+    return out
+
+
+def acoustic_rate(s):
+    """Damping rate of the longest sound mode along the sample, nu k^2 / 2 with
+    k = pi / L (a standing wave between the short walls; lattice units)."""
+    return 0.5 * nu_lattice(s.tau) * (math.pi / s.nx) ** 2
+
+
+def chapman_enskog_state(s, fields, eq_state):
+    """Stored (post-collision) state that streams to f^eq plus its first-order
+    Chapman-Enskog part: post_i(x) = f^eq_i(x + n_i) - (f^eq_i(x + n_i) - f^eq_i(x)) / omega_i(x),
+    omega_i = gamma (1 - v_i.u) / tau; where x + n_i lies outside the sample
+    the equilibrium at x is kept.  eq_state: the stored state of f^eq of the
+    fields (deviations f - w, [48][ny][nx]); half: see bound_seeds."""
+    n, ux, uy, T = fields
+    g = 1.0 / np.sqrt(1.0 - ux * ux - uy * uy)
+    out = np.empty_like(eq_state)
+    ny, nx = ux.shape
+    for d, (hx, hy) in enumerate(HOPS):
+        om = g * (1.0 - (hx * ux + hy * uy) / 5.0) / s.tau
+        for j in range(4):
+            i = 4 * d + j
+            e = eq_state[i]
+            sh = np.array(e)
+            ys = slice(max(0, -hy), ny - max(0, hy))
+            xs = slice(max(0, -hx), nx - max(0, hx))
+            yd = slice(max(0, hy), ny - max(0, -hy))
+            xd = slice(max(0, hx), nx - max(0, -hx))
+            sh[ys, xs] = e[yd, xd]           # f^eq_i(x + n_i) where it exists
+            out[i] = sh - (sh - e) / om
+    return out
+
+
+def bound_seeds(samples, prec="f64", check=25, max_steps=40000):
+    """Steps to residual <= TOL from the rest state and from seeds built out
+    of the exact steady fields (as f^eq, partly, and with the first-order
+    Chapman-Enskog part), plus the late decay rate of the residual against
+    the damping of the longest sound mode.  Yields one dict per seed."""
+    steps0, _, steady, _ = converge(samples, prec, check=check, max_steps=max_steps)
+    eq_states = []
+    import torch
+    for s, f in zip(samples, steady):
+        with rlbm.Solver(s, prec="f64") as sv:
+            sv.init(0, *[np.ascontiguousarray(a) for a in f])
+            eq_states.append(sv.get_state(0))
+        torch.cuda.synchronize()
+    one = lambda f: np.ones_like(f[0])
+    seeds = {
+        "rest (n = T = 1, u = 0)": dict(init=None),
+        "exact steady n, u, T as f^eq": dict(init=steady),
+        "exact steady n, u (T = 1)": dict(init=[(f[0], f[1], f[2], one(f)) for f in steady]),
+        "exact steady u (n = T = 1)": dict(init=[(one(f), f[1], f[2], one(f)) for f in steady]),
+        "exact fields + first-order Chapman-Enskog part": dict(
+            states=[chapman_enskog_state(s, f, e) for s, f, e in zip(samples, steady, eq_states)]),
+        "same, half the Chapman-Enskog part": dict(
+            states=[0.5 * (e + chapman_enskog_state(s, f, e)) for s, f, e in zip(samples, steady, eq_states)]),
+    }
+    ac = np.array([acoustic_rate(s) for s in samples])
+    for name, kw in seeds.items():
+        hist = []
+        st, _, _, _ = converge(samples, prec, check=check, max_steps=max_steps, history=hist, **kw)
+        lam = decay_rates(hist, check)
+        ok = np.isfinite(lam)
+        yield {"seed": name, "samples": len(samples), "precision": prec,
+               "steps_mean": float(st.mean()), "steps_median": float(np.median(st)),
+               "late_decay_rate_median": float(np.median(lam[ok])) if ok.any() else None,
+               "decay_rate_over_sound_damping_median": float(np.median(lam[ok] / ac[ok])) if ok.any() else None}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--samples", type=int, default=2000)
@@ -297,8 +398,15 @@ def main():
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--seed", type=int, default=20180406)
     ap.add_argument("--eval-samples", type=int, default=64)
+    ap.add_argument("--bound", type=int, default=0,
+                    help="instead of training: the seed bound on this many held-out samples")
     args = ap.parse_args()
     log = lambda m: print(m, flush=True)
+    if args.bound:
+        held = dataset_samples(args.samples + args.bound, args.seed)[args.samples:]
+        for line in bound_seeds(held):
+            log(json.dumps(line))
+        return
     cfg = fno.FNOConfig(N=args.canvas, C=args.width, Cq=4 * args.width, L=args.layers,
                         m1=args.modes, m2=args.modes)
     samples = dataset_samples(args.samples + args.test, args.seed)
