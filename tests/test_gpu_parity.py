@@ -288,3 +288,24 @@ def test_4096x2048_sample_one_step_in_windows(rl, prec):
         worst[(x0, y0)] = max(e.values())
         assert max(e.values()) < TOL[prec], ((x0, y0), e)
     print(f"4096 x 2048 {prec}: worst window error {max(worst.values()):.2e}")
+
+
+def test_fp32_state_continues_in_fp64(rl):
+    """The FP32-then-FP64 route to steady state: a state exported by an FP32
+    context and loaded into an FP64 context is the same state (to FP64
+    rounding), and one FP64 step from it equals the oracle's step from it."""
+    s = ragged_sample()
+    lat = lbm.Lattice(s)
+    fields = [np.ascontiguousarray(f) for f in W.random_fields(s, 13, du=0.05, dn=0.02, dT=0.02)]
+    with rl.Solver(s, prec="f32") as sv:
+        sv.init(0, *fields)
+        sv.step(40)
+        st32 = sv.get_state()
+    with rl.Solver(s, prec="f64") as sv:
+        sv.set_state(st32)
+        back = sv.get_state()
+        sv.step(1)
+        one = sv.get_state()
+        sv.check()
+    assert np.abs(back - st32).max() <= 4e-16 * np.abs(st32).max()
+    assert rel_err(one, lbm.step(lat, st32)) < 1e-13
