@@ -82,8 +82,15 @@ int rlbm_massive_create(const rlbm_massive_config* cfg, rlbm_massive_ctx** out);
 int rlbm_massive_init(rlbm_massive_ctx* ctx, const double* n, const double* ux,
                       const double* uy, const double* T, int device_ptrs);
 
-/* Advances by nsteps >= 0 time steps (one kernel launch each; asynchronous). */
-int rlbm_massive_step(rlbm_massive_ctx* ctx, int nsteps);
+/* Advances by nsteps >= 0 time steps (one kernel launch each; asynchronous
+ * when residual is NULL).  With residual != NULL (nsteps >= 1) the velocity
+ * field before and after the last step (Landau frame of the streamed
+ * populations, as rlbm_massive_moments) gives
+ *     *residual = ||u(t) - u(t-1)||_2 / ||u(t)||_2   over all sites
+ * (0 if both norms vanish, +inf if only ||u(t)|| does); the stream is then
+ * synchronised and the error word checked (RLBM_ENAN).  The residual uses
+ * 4 FP64 planes of context scratch, allocated on first use. */
+int rlbm_massive_step(rlbm_massive_ctx* ctx, int nsteps, double* residual);
 
 /* Landau-frame n, ux, uy, T of the streamed populations (the fields the next
  * collision uses).  Any output may be NULL. */

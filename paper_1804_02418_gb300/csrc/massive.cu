@@ -580,6 +580,29 @@ __global__ void k_mset(R* __restrict__ dst, MGeom geo, const double* __restrict_
   }
 }
 
+// sum over sites of |u - u_prev|^2 and |u|^2 into acc[0], acc[1] (FP64):
+// warp shuffles, one pair of atomics per warp
+__global__ void k_mresidual(const double* __restrict__ uxp, const double* __restrict__ uyp,
+                            const double* __restrict__ ux, const double* __restrict__ uy,
+                            long long nsite, double* __restrict__ acc) {
+  double a = 0.0, b = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nsite;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double dx = ux[t] - uxp[t], dy = uy[t] - uyp[t];
+    a = fma(dx, dx, fma(dy, dy, a));
+    b = fma(ux[t], ux[t], fma(uy[t], uy[t], b));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, a);
+    atomicAdd(acc + 1, b);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -680,6 +703,45 @@ int need_scratch(rlbm_massive_ctx* c, size_t bytes) {
 int grid_1d(long long work) {
   long long b = (work + 255) / 256;
   return (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+}
+
+}  // namespace
+
+namespace {
+
+int launch_steps(rlbm_massive_ctx* c, int nsteps) {
+  const bool force = c->cfg.Fx != 0.0 || c->cfg.Fy != 0.0;
+  const dim3 grid = grid_of(c->geo), block(32, 4);
+  for (int s = 0; s < nsteps; ++s) {
+    const void* src = c->buf[c->cur];
+    void* dst = c->buf[c->cur ^ 1];
+    if (c->elem == 8) {
+      const double it = 1.0 / c->cfg.tau, fx = c->cfg.Fx, fy = c->cfg.Fy;
+      if (force) k_mstep<double, true><<<grid, block, 0, stream_of(c)>>>((const double*)src, (double*)dst, c->geo, it, fx, fy, c->err);
+      else k_mstep<double, false><<<grid, block, 0, stream_of(c)>>>((const double*)src, (double*)dst, c->geo, it, fx, fy, c->err);
+    } else {
+      const float it = (float)(1.0 / c->cfg.tau), fx = (float)c->cfg.Fx, fy = (float)c->cfg.Fy;
+      if (force) k_mstep<float, true><<<grid, block, 0, stream_of(c)>>>((const float*)src, (float*)dst, c->geo, it, fx, fy, c->err);
+      else k_mstep<float, false><<<grid, block, 0, stream_of(c)>>>((const float*)src, (float*)dst, c->geo, it, fx, fy, c->err);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+    c->cur ^= 1;
+    ++c->steps;
+    ++c->launches;
+  }
+  return RLBM_OK;
+}
+
+int velocity_planes(rlbm_massive_ctx* c, double* ux, double* uy) {
+  if (c->elem == 8)
+    k_mmoments<double><<<grid_of(c->geo), dim3(32, 4), 0, stream_of(c)>>>((const double*)c->buf[c->cur], c->geo, nullptr, ux, uy, nullptr, c->err);
+  else
+    k_mmoments<float><<<grid_of(c->geo), dim3(32, 4), 0, stream_of(c)>>>((const float*)c->buf[c->cur], c->geo, nullptr, ux, uy, nullptr, c->err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+  ++c->launches;
+  return RLBM_OK;
 }
 
 }  // namespace
@@ -794,31 +856,37 @@ int rlbm_massive_init(rlbm_massive_ctx* c, const double* n, const double* ux, co
   return RLBM_OK;
 }
 
-int rlbm_massive_step(rlbm_massive_ctx* c, int nsteps) {
+
+
+int rlbm_massive_step(rlbm_massive_ctx* c, int nsteps, double* residual) {
   if (!c) return fail(nullptr, RLBM_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(c, RLBM_EINVAL, "nsteps < 0");
-  const bool force = c->cfg.Fx != 0.0 || c->cfg.Fy != 0.0;
-  const dim3 grid = grid_of(c->geo), block(32, 4);
-  for (int s = 0; s < nsteps; ++s) {
-    const void* src = c->buf[c->cur];
-    void* dst = c->buf[c->cur ^ 1];
-    if (c->elem == 8) {
-      const double it = 1.0 / c->cfg.tau, fx = c->cfg.Fx, fy = c->cfg.Fy;
-      if (force) k_mstep<double, true><<<grid, block, 0, stream_of(c)>>>((const double*)src, (double*)dst, c->geo, it, fx, fy, c->err);
-      else k_mstep<double, false><<<grid, block, 0, stream_of(c)>>>((const double*)src, (double*)dst, c->geo, it, fx, fy, c->err);
-    } else {
-      const float it = (float)(1.0 / c->cfg.tau), fx = (float)c->cfg.Fx, fy = (float)c->cfg.Fy;
-      if (force) k_mstep<float, true><<<grid, block, 0, stream_of(c)>>>((const float*)src, (float*)dst, c->geo, it, fx, fy, c->err);
-      else k_mstep<float, false><<<grid, block, 0, stream_of(c)>>>((const float*)src, (float*)dst, c->geo, it, fx, fy, c->err);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
-    c->cur ^= 1;
-    ++c->steps;
-    ++c->launches;
-  }
-  return RLBM_OK;
+  if (!residual) return launch_steps(c, nsteps);
+  if (nsteps < 1) return fail(c, RLBM_EINVAL, "a residual needs nsteps >= 1");
+  const long long ns = (long long)c->geo.nx * c->geo.ny;
+  int r = need_scratch(c, 4 * ns * sizeof(double) + 2 * sizeof(double));
+  if (r) return r;
+  double* up = c->scratch;             // u(t - 1): x, y planes; u(t): x, y planes; sums
+  double* acc = c->scratch + 4 * ns;
+  if ((r = launch_steps(c, nsteps - 1))) return r;
+  if ((r = velocity_planes(c, up, up + ns))) return r;
+  if ((r = launch_steps(c, 1))) return r;
+  if ((r = velocity_planes(c, up + 2 * ns, up + 3 * ns))) return r;
+  cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), stream_of(c));
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  k_mresidual<<<grid_1d(ns), 256, 0, stream_of(c)>>>(up, up + ns, up + 2 * ns, up + 3 * ns, ns, acc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "residual kernel");
+  ++c->launches;
+  double h[2];
+  e = cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, stream_of(c));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream_of(c));
+  if (e != cudaSuccess) return cuda_fail(c, e, "residual readback");
+  *residual = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : (h[0] > 0.0 ? INFINITY : 0.0);
+  return rlbm_massive_check(c);
 }
+
+
 
 int rlbm_massive_moments(rlbm_massive_ctx* c, double* n, double* ux, double* uy, double* T,
                          int device_ptrs) {

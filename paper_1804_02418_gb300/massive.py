@@ -30,7 +30,7 @@ _EXPORTS = {
     "rlbm_massive_stencil": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)] * 2),
     "rlbm_massive_create": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.POINTER(_P)]),
     "rlbm_massive_init": (ctypes.c_int, [_P] * 5 + [ctypes.c_int]),
-    "rlbm_massive_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "rlbm_massive_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rlbm_massive_moments": (ctypes.c_int, [_P] * 5 + [ctypes.c_int]),
     "rlbm_massive_get_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "rlbm_massive_set_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -126,8 +126,15 @@ class MassiveSolver:
         args = [ctypes.c_void_p(p[0]) if p[0] is not None else None for p in ptrs]
         self._check(self.lib.rlbm_massive_init(self.ctx, *args, int(bool(dev))))
 
-    def step(self, nsteps: int):
-        self._check(self.lib.rlbm_massive_step(self.ctx, int(nsteps)))
+    def step(self, nsteps: int, residual: bool = False):
+        """Advances nsteps; with residual=True returns ||u(t) - u(t-1)|| / ||u(t)||
+        over the last step (synchronises)."""
+        if residual:
+            r = ctypes.c_double()
+            self._check(self.lib.rlbm_massive_step(self.ctx, int(nsteps), ctypes.byref(r)))
+            return r.value
+        self._check(self.lib.rlbm_massive_step(self.ctx, int(nsteps), None))
+        return None
 
     def moments(self, out=None):
         """(n, ux, uy, T): host numpy arrays [ny][nx], or into `out` (four

@@ -231,3 +231,29 @@ def test_checkpoint_and_resume(ms, prec):
         assert np.array_equal(resumed, full)          # the restored state is bit-identical
     else:
         assert np.abs(resumed - full).max() <= 1e-13 * np.abs(full).max()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-3)])
+def test_residual_matches_the_oracle(ms, prec, tol):
+    """r = ||u(t) - u(t-1)|| / ||u(t)|| over the last of 12 steps, against the
+    same quantity from two consecutive oracle fields."""
+    nx, ny = 40, 27
+    f = random_fields(nx, ny, 31)
+    lat = M.Lattice(nx, ny, True, False, 0.9, 1e-5, 0.0)
+    post = M.run(lat, M.init(lat, *f), 11)
+    u0 = M.fields(lat, post)
+    u1 = M.fields(lat, M.step(lat, post))
+    ref = np.sqrt(((u1[1] - u0[1]) ** 2 + (u1[2] - u0[2]) ** 2).sum() / (u1[1] ** 2 + u1[2] ** 2).sum())
+    with ms.MassiveSolver(nx, ny, True, False, 0.9, 1e-5, 0.0, prec=prec) as sv:
+        sv.init(*f)
+        r = sv.step(12, residual=True)
+        assert sv.steps_done == 12
+        got = sv.moments()
+    assert abs(r / ref - 1) < tol, (r, ref)
+    assert normwise(got, u1) < (1e-12 if prec == "f64" else 1e-5)
+    # a residual over a single step is allowed, zero steps is not
+    with ms.MassiveSolver(nx, ny, True, False, 0.9, prec=prec) as sv:
+        sv.init()
+        assert sv.step(1, residual=True) == 0.0        # the rest state does not move
+        with pytest.raises(Exception):
+            sv.step(0, residual=True)
