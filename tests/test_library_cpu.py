@@ -167,3 +167,34 @@ def test_chapman_enskog_seed_matches_its_definition():
                     assert out[i, y, x] == pytest.approx(want, rel=1e-14, abs=1e-15)
     h = [np.array([1e-3, 2e-3]) * np.exp(-0.01 * 25 * k) for k in range(1, 60)]
     assert np.allclose(ws.decay_rates(h, 25), 0.01, rtol=1e-10)
+
+
+def test_c_abi_from_plain_c(lib, tmp_path):
+    """A C program linked against librlbm.so (no Python, no torch) gets the
+    same quadratures as the oracle and the same argument checks."""
+    import shutil
+    import subprocess
+    from oracle import massive as M
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.join(ROOT, "paper_1804_02418_gb300", "lib")
+    exe = str(tmp_path / "host_calls")
+    r = subprocess.run([cc, os.path.join(ROOT, "tests", "c_abi", "host_calls.c"),
+                        "-I", os.path.join(ROOT, "include"), "-L", libdir, "-lrlbm",
+                        "-Wl,-rpath," + libdir, "-Wl,--allow-shlib-undefined", "-o", exe],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    lines = {l.split()[0]: l.split()[1:] for l in out.stdout.splitlines()}
+    w1, w2, p0 = rlbm.quadrature()
+    rc, a, b, c = lines["quadrature"]
+    assert rc == "0" and float(a) == w1[0] and float(b) == w2[0] and float(c) == p0[1]
+    q = M.quadrature()
+    rc, v0, lo, hi, w0 = lines["massive_quadrature"]
+    assert rc == "0" and float(v0) == q["v0"] and float(w0) == pytest.approx(q["w_class"][0], rel=1e-13)
+    assert lines["stencil"] == ["0", "1", "0", "0", "0"]
+    assert lines["massive_create_bad"] == ["-1", "1", "msg"]
+    assert lines["workspace_bad"] == ["-1", "msg"]
+    assert lines["workspace_ok"][0] == "0" and int(lines["workspace_ok"][1]) >= 2 * 48 * 64 * 32 * 4
