@@ -20,9 +20,15 @@
 // race on it and must be serialised by the caller.
 //
 // Host code must not pass the array's name to a kernel: on the host it is
-// only a stand-in symbol.  The device address is looked up once per device
-// with cudaGetSymbolAddress, by the first call made while that device is
-// current; make that first call before any stream capture begins.
+// only a stand-in symbol.  Its device address belongs to the CUDA context
+// that loaded the library's module, so every call made outside a stream
+// capture looks it up again with cudaGetSymbolAddress (which allocates
+// nothing) in the context current at that moment; a pointer kept from an
+// earlier context (before cudaDeviceReset, or another context on the same
+// device) is never used.  A call made while its stream is being captured
+// cannot look it up and takes the address the last uncaptured call on the
+// same device found: make one call outside capture first, and again after
+// cudaDeviceReset or a change of context, before capturing.
 #include "rlbm.h"
 
 #include <cuda_runtime.h>
@@ -129,10 +135,22 @@ extern "C" int rlbm_velocity_residual_static(const double* ux_prev, const double
   if (e != cudaSuccess) return fail(RLBM_ECUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices)
     return fail(RLBM_EINVAL, "rlbm_velocity_residual_static: device index out of range");
-  double* scratch;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Is the stream being captured?  An error (e.g. the legacy stream while
+  // another stream captures globally) counts as capturing: no lookup then.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  bool capturing = false;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    (void)cudaGetLastError();
+    capturing = true;
+  } else {
+    capturing = cs != cudaStreamCaptureStatusNone;
+  }
+  double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch[dev]) {
+    if (!capturing) {
+      // the address in the context that is current now (never a kept one)
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_res_partials);
       if (e != cudaSuccess || !p) {
@@ -142,11 +160,14 @@ extern "C" int rlbm_velocity_residual_static(const double* ux_prev, const double
         return fail(RLBM_ECUDA, b);
       }
       g_scratch[dev] = static_cast<double*>(p);
+    } else if (!g_scratch[dev]) {
+      return fail(RLBM_ESTATE,
+                  "rlbm_velocity_residual_static: first call on this device inside a stream "
+                  "capture; make one call outside capture first");
     }
     scratch = g_scratch[dev];
   }
   const int nblocks = (int)((nsites + kResTile - 1) / kResTile);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   k_res_partial<<<nblocks, kResThreads, 0, st>>>(ux_prev, uy_prev, ux, uy, nsites, scratch);
   k_res_final<<<1, kResThreads, 0, st>>>(scratch, nblocks, residual);
   e = cudaGetLastError();

@@ -81,6 +81,32 @@ def test_static_residual_matches_rlbm_step_on_two_calls_in_a_row(env):
         assert abs(got - ref) <= RTOL * ref, (steps, got, ref)
 
 
+def torch_residual(torch, uxp, uyp, ux, uy):
+    """The same quantity by torch float64 reductions (another summation order)."""
+    du2 = ((ux - uxp) ** 2 + (uy - uyp) ** 2).sum()
+    u2 = (ux ** 2 + uy ** 2).sum()
+    return float(torch.sqrt(du2 / u2).item())
+
+
+def test_static_residual_large_maximum_then_small_sizes(env):
+    """Paths the 150 x 77 case does not reach: more partial blocks than the
+    final kernel's threads (strided final loop), the largest accepted size
+    (every scratch slot written), and a small call right after a large one
+    (slots beyond its own block count must not be read)."""
+    torch, rlbm = env
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(7)
+    for n in (1_500_001, 8_388_608, 333, 2048, 2049):
+        uxp, uyp = (1e-3 * torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+                    for _ in range(2))
+        ux = uxp + 1e-6 * torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+        uy = uyp + 1e-6 * torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+        ref = torch_residual(torch, uxp, uyp, ux, uy)
+        got = static_residual(torch, rlbm, uxp, uyp, ux, uy, out)
+        assert abs(got - ref) <= 1e-12 * ref, (n, got, ref)
+        del uxp, uyp, ux, uy
+
+
 def test_static_residual_rejects_sizes_beyond_its_scratch(env):
     torch, rlbm = env
     lib = rlbm.load_library()
