@@ -14,7 +14,13 @@ solve, equilibrium, forcing and relaxation, all in one kernel launch.
 L2: the working set of one step (read 48 planes, write 48 planes) is larger
 than L2 only in FP64, so a buffer larger than L2 is written before every
 timed step and each step is timed alone with CUDA events on the library's
-stream; `value` sums those device times.
+stream; `value` sums those device times.  `back_to_back` times the same K steps
+in one event pair without flushes (each step's write-backs inside the timed
+region).
+
+Clocks: NVML is read every ~2 ms by a background thread from before the
+warm-up to after the e2e leg; the line reports the median SM clock inside the
+timed region and refuses to print without any sample.
 
 e2e: the same metric through the C ABI with pinned host buffers: upload of
 the initial fields, the K steps and the read-back of (n, u_x, u_y, T), all
@@ -110,6 +116,19 @@ def ncu_traffic(prec):
     if not e or prec not in KERNEL_SOURCES or e.get("source_hash") != source_hash(prec):
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def ncu_fp64_per_site():
+    """FP64-pipe thread instructions per site update of the FP64 step kernel
+    from the committed ncu capture, or None when its sources changed since."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        e = json.load(f).get("f64")
+    if not e or e.get("source_hash") != source_hash("f64"):
+        return None
+    return e.get("fp64_instructions_per_site")
 
 
 # ---------------------------------------------------------------------------
@@ -310,53 +329,129 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 
 class Clocks:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and throttle reasons sampled DURING the run by a background
+    thread: NVML through ctypes every ~2 ms (nvidia-smi every 50 ms if NVML
+    cannot be loaded), from before the warm-up to after the e2e leg.
+    `mark(name)` stamps the host time; `stop()` reports the median SM clock of
+    the samples taken inside the device-timed window (marks "timed0" ..
+    "timed1", host stamps around the enqueue and the closing synchronize),
+    and of all samples.  Reading clocks changes no GPU setting."""
+    # NVML clocks-event-reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, index):
+        import threading
         self.index = index
-        self.proc = None
-        self.path = os.path.join(tempfile.gettempdir(), f"bench_clocks_{os.getpid()}.csv")
+        self.samples = []          # (t, sm_mhz, max_mhz, reasons bitmask)
+        self.marks = {}
+        self._stop = threading.Event()
+        self._thread = None
+        self.source = None
+
+    def _nvml(self):
+        import ctypes
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                lib = None
+        if lib is None or lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        idx = self.index
+        try:
+            import torch
+            idx = torch.cuda._get_nvml_device_index(self.index)
+        except Exception:
+            pass
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(h)) != 0:
+            return None
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+
+        def read():
+            mhz, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) != 0:   # NVML_CLOCK_SM
+                return None
+            lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+            reasons_fn(h, ctypes.byref(rs))
+            return float(mhz.value), float(mx.value), int(rs.value)
+        return read
+
+    def _run_nvml(self, read):
+        while not self._stop.is_set():
+            r = read()
+            if r is not None:
+                self.samples.append((time.perf_counter(),) + r)
+            self._stop.wait(0.002)
+
+    def _run_smi(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        bits = [0x8, 0x40, 0x20, 0x4]
+        try:
+            p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                  "--format=csv,noheader,nounits", "-lms", "50"],
+                                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            return
+        self._smi = p
+        for line in p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            try:
+                mask = sum(b for b, v in zip(bits, parts[2:6]) if v.lower() == "active")
+                self.samples.append((time.perf_counter(), float(parts[0]), float(parts[1]), mask))
+            except (ValueError, IndexError):
+                continue
+            if self._stop.is_set():
+                break
 
     def start(self):
+        import threading
+        read = None
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
-                stderr=subprocess.DEVNULL)
+            read = self._nvml()
         except Exception:
-            self.proc = None
+            read = None
+        if read is not None:
+            self.source = "nvml, ~2 ms"
+            self._thread = threading.Thread(target=self._run_nvml, args=(read,), daemon=True)
+        else:
+            self.source = "nvidia-smi, 50 ms"
+            self._thread = threading.Thread(target=self._run_smi, daemon=True)
+        self._thread.start()
+        time.sleep(0.05)
+
+    def mark(self, name):
+        self.marks[name] = time.perf_counter()
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax = float(parts[2])
-                except ValueError:
-                    continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
-        sm.sort()
-        med = sm[len(sm) // 2] if sm else None
-        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+        time.sleep(0.02)
+        self._stop.set()
+        p = getattr(self, "_smi", None)
+        if p is not None:
+            p.terminate()
+        if self._thread is not None:
+            self._thread.join(timeout=5)
+        t0, t1 = self.marks.get("timed0"), self.marks.get("timed1")
+        timed = [x for x in self.samples if t0 is not None and t1 is not None and t0 <= x[0] <= t1]
+        use = timed if timed else self.samples
+        if not use:
+            raise SystemExit("bench: no clock sample was taken (NVML and nvidia-smi unavailable); "
+                             "refusing to print a line without a clock record")
+        sm = sorted(x[1] for x in use)
+        every = sorted(x[1] for x in self.samples)
+        reasons = sorted({nm for x in use for b, nm in self.REASONS.items() if x[3] & b})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(x[2] for x in use),
+                "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(timed),
+                "samples_whole_run": len(self.samples),
+                "sm_mhz_whole_run_median": every[len(every) // 2],
+                "sm_mhz_whole_run_min": every[0], "source": self.source,
+                "window": "device-timed region" if timed else
+                          "whole GPU phase (warm-up .. e2e): no sample fell inside the timed region"}
 
 
 def gpu_arm(args, rank, world, cpu_line):
@@ -396,6 +491,9 @@ def gpu_arm(args, rank, world, cpu_line):
         if world > 1:
             dist.barrier()
 
+    # clocks are sampled from before the warm-up to the end of the e2e leg
+    clocks = Clocks(local)
+    clocks.start()
     # -- device-timed region: K single steps, L2 flushed before each ----------
     with torch.cuda.stream(stream):
         sv.init(0)
@@ -405,10 +503,9 @@ def gpu_arm(args, rank, world, cpu_line):
     sync_all()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clocks = Clocks(local)
-    clocks.start()
     l0 = sv.launches
     sync_all()
+    clocks.mark("timed0")
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush_l2()
@@ -416,11 +513,22 @@ def gpu_arm(args, rank, world, cpu_line):
             sv.step(1)
             ev[k][1].record(stream)
     sync_all()
+    clocks.mark("timed1")
     launches = sv.launches - l0
-    clk = clocks.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     sv.check()
     t_ms = parallel.max_over_ranks(t_ms, device="cuda")
+
+    # -- the same K steps back to back in one event pair, no flush: every
+    # step's write-backs fall inside the timed region -------------------------
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sync_all()
+    b0.record(stream)
+    sv.step(args.steps)
+    b1.record(stream)
+    sync_all()
+    b2b_ms = parallel.max_over_ranks(b0.elapsed_time(b1), device="cuda")
+    sv.check()
 
     # -- end to end through the C ABI with pinned host buffers ----------------
     host_in = [torch.ones((s.ny, s.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
@@ -437,6 +545,8 @@ def gpu_arm(args, rank, world, cpu_line):
     sync_all()
     e2e_ms = parallel.max_over_ranks(e0.elapsed_time(e1), device="cuda")
     finite = bool(np.isfinite(host_out[1].numpy()).all())
+    clk = clocks.stop()
+    fma_peak = rlbm.fma_peak(True) if args.prec == "f64" else None
     sv.close()
 
     if rank != 0:
@@ -447,6 +557,21 @@ def gpu_arm(args, rank, world, cpu_line):
     achieved = alg_bytes / avg_launch_s / 1e9
     value = world * sites * args.steps / (t_ms / 1e3) / 1e9
     field_bytes = 4 * 8 * sites
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": ncu_traffic(args.prec), "peak_kind": hbm_kind,
+            "algorithmic_bytes_per_launch": alg_bytes}
+    if args.prec == "f64":
+        # FP64 arithmetic, not HBM, bounds this path: FP64-pipe instructions per
+        # site (committed ncu count) x sites / launch time against the FP64 FMA
+        # rate the library's probe measures on this GPU now
+        per_site = ncu_fp64_per_site()
+        ach = per_site * sites / avg_launch_s / 1e9 if per_site else None
+        roof = {"bound": "alu", "achieved": ach, "peak": fma_peak / 1e9,
+                "unit": "G FP64 instructions/s", "frac": ach / (fma_peak / 1e9) if ach else None,
+                "traffic": ncu_traffic(args.prec), "peak_kind": "measured (rlbm_fma_peak probe, "
+                "FP64 FMA chains on every SM, this run)",
+                "fp64_instructions_per_site": per_site,
+                "hbm": {"achieved": achieved, "peak": hbm, "frac": achieved / hbm}}
     line = {
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
@@ -461,15 +586,20 @@ def gpu_arm(args, rank, world, cpu_line):
                                               ("batched, staged pulls" if shape[2] else "batched")},
                    "l2": "before every timed step a 2x L2 buffer is written, then another 2x L2 buffer read (cold L2, no pending write-backs); steps timed alone",
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": ncu_traffic(args.prec),
-                     "peak_kind": hbm_kind,
-                     "algorithmic_bytes_per_launch": alg_bytes},
+        "roofline": roof,
+        "back_to_back": {"value": world * sites * args.steps / (b2b_ms / 1e3) / 1e9,
+                         "unit": "GLUPS", "ms_per_step": b2b_ms / args.steps,
+                         "frac_of_hbm_peak": alg_bytes * args.steps / (b2b_ms / 1e3) / 1e9 / hbm,
+                         "note": "the same K steps in one event pair, no L2 flush: each step's "
+                                 "write-backs land inside the timed region"},
         "e2e": {"value": world * sites * args.steps / (e2e_ms / 1e3) / 1e9, "unit": "GLUPS",
                 "h2d_bytes_per_step": field_bytes / args.steps,
-                "d2h_bytes_per_step": field_bytes / args.steps},
+                "d2h_bytes_per_step": field_bytes / args.steps,
+                "note": f"init from pinned host fields + {args.steps} steps + read-back of four "
+                        "FP64 fields in one event pair"},
         "gpu_launches": launches,
         "clocks": clk,
+        "ms_per_step_x_sm_mhz": t_ms / args.steps * clk["sm_mhz"],
         "fields_finite": finite,
     }
     if cpu_line is not None:
@@ -513,6 +643,8 @@ def massive_arm(args, rank, world, cpu_line):
             import torch.distributed as dist
             dist.barrier()
 
+    clocks = Clocks(local)
+    clocks.start()
     with torch.cuda.stream(stream):
         sv.init()
         for _ in range(args.warmup):
@@ -521,10 +653,9 @@ def massive_arm(args, rank, world, cpu_line):
     sync_all()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clocks = Clocks(local)
-    clocks.start()
     l0 = sv.launches
     sync_all()
+    clocks.mark("timed0")
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush_l2()
@@ -532,8 +663,8 @@ def massive_arm(args, rank, world, cpu_line):
             sv.step(1)
             ev[k][1].record(stream)
     sync_all()
+    clocks.mark("timed1")
     launches = sv.launches - l0
-    clk = clocks.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     sv.check()
     t_ms = parallel.max_over_ranks(t_ms, device="cuda")
@@ -553,6 +684,7 @@ def massive_arm(args, rank, world, cpu_line):
     e2e_ms = parallel.max_over_ranks(e0.elapsed_time(e1), device="cuda")
     finite = bool(np.isfinite(host_out[1].numpy()).all())
     sv.check()
+    clk = clocks.stop()
     sv.close()
     if rank != 0:
         return
@@ -616,20 +748,21 @@ def ensemble_arm(args, rank, world):
         if world > 1:
             dist.barrier()
 
+    clocks = Clocks(local)
+    clocks.start()
     with torch.cuda.stream(stream):
         sv.step(args.warmup)
     sync_all()
-    clocks = Clocks(local)
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = sv.launches
     sync_all()
+    clocks.mark("timed0")
     e0.record(stream)
     sv.step(args.steps)
     e1.record(stream)
     sync_all()
+    clocks.mark("timed1")
     launches = sv.launches - l0
-    clk = clocks.stop()
     t_s = e0.elapsed_time(e1) / 1e3
     sv.check()
     value = parallel.job_throughput(sites * args.steps, t_s, device="cuda") / 1e9
@@ -641,6 +774,7 @@ def ensemble_arm(args, rank, world):
     res = sv.sample_residuals()
     w1 = time.perf_counter()
     e2e = parallel.job_throughput(sites * args.steps, w1 - w0, device="cuda") / 1e9
+    clk = clocks.stop()
     sv.close()
     if rank != 0:
         return

@@ -137,6 +137,24 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out);
 int rlbm_init(rlbm_ctx* ctx, int sample, const double* n, const double* ux,
               const double* uy, const double* T, int device_ptrs);
 
+/* Sets the stored state of `sample` to the Chapman-Enskog seed of the given
+ * fields: the state whose first pull-stream yields, at every site x and
+ * population i whose source x - n_i lies in the sample (or wraps on a
+ * periodic axis), the equilibrium plus its first-order non-equilibrium part
+ * of a steady flow,
+ *     f_i(x) = f^eq_i(x) - (f^eq_i(x) - f^eq_i(x - n_i)) / omega_i(x),
+ *     omega_i = gamma (1 - v_i.u) / tau,
+ * i.e. Eq. discrete-rbe in steady state with f - f^eq small and slowly
+ * varying (the paper states no seed; this is the library's reading).  The
+ * stored value of population i at site s is f^eq_i(d) - (f^eq_i(d) -
+ * f^eq_i(s)) / omega_i(d), d = s + n_i, or f^eq_i(s) where d is outside the
+ * sample.  Its non-equilibrium shear stress is the first-order (Navier-
+ * Stokes) stress of the relaxation-time model, eta = (3/4) n T tau.  Same
+ * arguments, layout and checks as rlbm_init (NULL fields: the rest state);
+ * with the electric force on, the first step's density is n. */
+int rlbm_init_ce(rlbm_ctx* ctx, int sample, const double* n, const double* ux,
+                 const double* uy, const double* T, int device_ptrs);
+
 /* Advances every sample by nsteps >= 0 time steps (stream, then collide).
  * If residual != NULL, the last two steps also reduce
  *   r = ||u(t) - u(t-1)||_2 / ||u(t)||_2   over all sites of all samples
@@ -173,6 +191,15 @@ int rlbm_autotune(rlbm_ctx* ctx, int* bx, int* grid, int* staged);
  * Every shape runs the same per-site arithmetic (results agree to the last
  * bits; the code generator may contract multiply-adds differently per kernel). */
 int rlbm_set_launch_shape(rlbm_ctx* ctx, int bx, int grid, int staged);
+
+/* Failure detection: the longest a bounded device wait of this context may
+ * take, in GPU clock cycles (0, the default, means about one second).  It
+ * applies to the staged-pull kernel's waits for a tile's bulk copies; a wait
+ * that gives up sets the device error word's timeout bit (rlbm_check then
+ * returns RLBM_ETIMEOUT), the block still waits, bounded by the default, for
+ * the copies it has issued, and leaves the step incomplete: the state must be
+ * set again (rlbm_init / rlbm_set_state) before stepping on.  cycles >= 0. */
+int rlbm_set_wait_limit(rlbm_ctx* ctx, long long cycles);
 
 /* Macroscopic fields (n, u_x, u_y, T) of `sample` at the current time: the
  * Landau-frame values of the streamed populations, i.e. those the next
@@ -216,6 +243,15 @@ long long rlbm_launch_count(const rlbm_ctx* ctx);
 
 int rlbm_version(void);
 
+/* Measurement utility (no counterpart in the paper): the rate at which the
+ * current device retires fused multiply-adds of one type, FP64 (fp64 != 0)
+ * or FP32, from a kernel of independent FMA chains on every SM (best of three
+ * timed launches, CUDA events, a few milliseconds each).  *fma_per_s receives
+ * thread-level FMA instructions per second (flops / 2).  It is the peak the
+ * FP64 step, which is bound by its FP64 instructions, is compared with.
+ * Allocates a small output buffer and a stream; changes no device setting. */
+int rlbm_fma_peak(int fp64, double* fma_per_s);
+
 /* Convergence residual that allocates nothing (no counterpart in the paper).
  *
  * For callers that cannot allocate device memory when they check convergence
@@ -229,11 +265,16 @@ int rlbm_version(void);
  * Scratch is a fixed 64 KiB array inside the library (one partial-sum pair
  * per 2048 sites); nsites must be 1 .. 8,388,608, larger sizes return
  * RLBM_EINVAL with a message in rlbm_last_error(NULL).  Calls no
- * cudaMalloc, cudaFree or allocating library routine.  The first call on a
- * device (with that device current) looks the scratch address up; make it
- * before any stream capture.  All calls share the scratch: calls that
- * overlap on the GPU race and must be serialised by the caller.  The result
- * is the same quantity rlbm_step reports, summed in a fixed order. */
+ * cudaMalloc, cudaFree or allocating library routine.  Every call made
+ * outside a stream capture looks the scratch address up in the context
+ * current at that moment (cudaGetSymbolAddress); a call inside a capture
+ * reuses the address the last uncaptured call on the same device found, so
+ * make one call outside capture before capturing, and again after
+ * cudaDeviceReset or a switch to another context on that device (a first
+ * call inside a capture returns RLBM_ESTATE).  All calls share the scratch:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * The result is the same quantity rlbm_step reports, summed in a fixed
+ * order. */
 int rlbm_velocity_residual_static(const double* ux_prev, const double* uy_prev,
                                   const double* ux, const double* uy, long long nsites,
                                   double* residual, void* stream);

@@ -23,7 +23,7 @@ LIB = os.path.join(LIBDIR, "librlbm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "quadrature.cpp", "kernels_f64.cu", "kernels_f32.cu",
-           "kernels_f16.cu", "kernels_bf16.cu", "residual_static.cu",
+           "kernels_f16.cu", "kernels_bf16.cu", "residual_static.cu", "probe.cu",
            "fno_kernels.cu", "massive_quadrature.cpp", "massive.cu"]
 
 

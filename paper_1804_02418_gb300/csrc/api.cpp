@@ -125,6 +125,7 @@ struct rlbm_ctx {
   // with pulls staged in shared memory by bulk copies if `staged` is 1
   int bx, grid;
   int staged;
+  long long wait_limit;       // cycles a bounded device wait may take (0: the default)
   int graph_steps;
   std::string tune_cache;
   cudaGraphExec_t graph[2];   // graph_steps steps starting from buffer 0 / 1
@@ -383,6 +384,7 @@ cudaError_t launch_step(rlbm_ctx* c, int from, int res, int bx, int grid, int st
   a.nsamples = (int)c->samples.size();
   a.cur = from;
   a.ntiles = c->ntiles[b];
+  a.wait_limit = c->wait_limit > 0 ? c->wait_limit : kStageSpinCycles;
   const int g = grid > 0 ? grid : (int)std::min<long long>(a.ntiles, 1LL << 30);
   cudaError_t e = c->ops->step_batch(c->ws, a, c->ws + c->ghost_off, c->force_any, res, bx, g,
                                      staged, uprev, acc, err, c->stream);
@@ -550,6 +552,7 @@ int rlbm_create(const rlbm_config* cfg, rlbm_ctx** out) {
   c->bx = c->samples.size() == 1 ? 0 : 128;
   c->grid = c->samples.size() == 1 ? 0 : (int)std::min<long long>(c->ntiles[1], 1LL << 30);
   c->staged = 0;
+  c->wait_limit = 0;
   *out = c;
   return RLBM_OK;
 }
@@ -571,8 +574,11 @@ const char* rlbm_last_error(const rlbm_ctx* c) {
 long long rlbm_steps_done(const rlbm_ctx* c) { return c ? c->steps : -1; }
 long long rlbm_launch_count(const rlbm_ctx* c) { return c ? c->launches : -1; }
 
-int rlbm_init(rlbm_ctx* c, int sample, const double* n, const double* ux, const double* uy,
-              const double* T, int device_ptrs) {
+namespace {
+
+// rlbm_init (ce = false) and rlbm_init_ce (ce = true)
+int init_sample(rlbm_ctx* c, int sample, const double* n, const double* ux, const double* uy,
+                const double* T, int device_ptrs, bool ce) {
   int r = check_sample_index(c, sample);
   if (r) return r;
   const int nnull = !n + !ux + !uy + !T;
@@ -599,8 +605,8 @@ int rlbm_init(rlbm_ctx* c, int sample, const double* n, const double* ux, const 
     }
     DevSample d = L.dev;
     d.cur = c->cur;      // the electric force's first step reads this density plane
-    e = c->ops->init(dst, d, dp[0], dp[1], dp[2], dp[3], at<unsigned>(c, c->err_off),
-                     c->stream);
+    e = (ce ? c->ops->init_ce : c->ops->init)(dst, d, dp[0], dp[1], dp[2], dp[3],
+                                              at<unsigned>(c, c->err_off), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     c->launches++;
   }
@@ -609,6 +615,18 @@ int rlbm_init(rlbm_ctx* c, int sample, const double* n, const double* ux, const 
                                [](char v) { return v != 0; });
   c->steps = 0;
   return RLBM_OK;
+}
+
+}  // namespace
+
+int rlbm_init(rlbm_ctx* c, int sample, const double* n, const double* ux, const double* uy,
+              const double* T, int device_ptrs) {
+  return init_sample(c, sample, n, ux, uy, T, device_ptrs, false);
+}
+
+int rlbm_init_ce(rlbm_ctx* c, int sample, const double* n, const double* ux, const double* uy,
+                 const double* T, int device_ptrs) {
+  return init_sample(c, sample, n, ux, uy, T, device_ptrs, true);
 }
 
 int rlbm_step(rlbm_ctx* c, int nsteps, double* residual) {
@@ -683,6 +701,14 @@ bool valid_shape(int bx, int grid, int staged) {
   return !(bx == 0 && (grid != 0 || staged));
 }
 }  // namespace
+
+int rlbm_set_wait_limit(rlbm_ctx* c, long long cycles) {
+  if (!c) return RLBM_EINVAL;
+  if (cycles < 0) return fail(c, RLBM_EINVAL, "wait limit %lld < 0", cycles);
+  c->wait_limit = cycles;
+  drop_graphs(c);             // captured launches carry the old limit
+  return RLBM_OK;
+}
 
 int rlbm_set_launch_shape(rlbm_ctx* c, int bx, int grid, int staged) {
   if (!c) return RLBM_EINVAL;

@@ -159,18 +159,26 @@ __device__ __forceinline__ void stage_bar_init(uint32_t bar, uint32_t count) {
 }
 
 
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the completion of the phase with the given parity: gives
+// up (false) once more than `limit` clock cycles have passed.  The first probe
+// does not block (test_wait), so a limit shorter than a copy's latency gives up
+// at once; later probes may suspend the thread for a while (try_wait).
+__device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity,
+                                           long long limit = kStageSpinCycles) {
   const long long t0 = clock64();
-  while (true) {
-    uint32_t ok;
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  while (!ok) {
+    if (clock64() - t0 > limit) return false;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > kStageSpinCycles) return false;
   }
+  return true;
 }
 
 // Issued by the 32 lanes of one warp (lane d < 12 copies direction d): the
@@ -392,6 +400,214 @@ __device__ __forceinline__ void gather(const S* __restrict__ fin, const DevSampl
   }
 }
 
+// Per-direction cubic coefficients of a direction pair, on lanes (d, d + 1):
+// the quantities pair_cubics() computes, written on register pairs.  Every
+// polynomial in v is split into even and odd parts, and the odd parts take
+// the constant pairs (a, -a) of QuadConsts::odd, so each instruction serves
+// both directions.  nT, nmT as in pair_cubics; FxT, FyT = (Fx, Fy) nT.
+// Returns R0..R3 (lanes p, n) and om = (omega_p, omega_n).
+template <bool FORCE, class C>
+__device__ __forceinline__ void pair_cubics_paired(const int d, const EqCoeffs<float>& c,
+                                                   float nT, float nmT, float gt, float gux,
+                                                   float guy, float FxT, float FyT, const C& qc,
+                                                   float2 (&R)[4], float2& om) {
+  const int q = d / 2;
+  const bool hx = hop_x(d) != 0, hy = hop_y(d) != 0;
+  const float vx = float(hop_x(d)) / 5.f, vy = float(hop_y(d)) / 5.f;
+  const float2* od = qc.odd[q];
+  // omega = gamma (1 -+ v.u) / tau on the two lanes
+  om = S2(gt);
+  if (hx) om = fma2(S2(gux), od[kONVx], om);
+  if (hy) om = fma2(S2(guy), od[kONVy], om);
+  const float2 on = mul2(om, S2(nT));
+  float2 q1 = S2(c.c1_0);
+  if (hx) q1 = fma2(S2(c.c1_x), od[kOVx], q1);
+  if (hy) q1 = fma2(S2(c.c1_y), od[kOVy], q1);
+  float2 q2 = S2(c.c2_0);
+  if (hx) q2 = fma2(S2(c.c2_xx), S2(vx * vx), q2);
+  if (hx && hy) q2 = fma2(S2(c.c2_xy), S2(vx * vy), q2);
+  if (hx) q2 = fma2(S2(c.c2_x), od[kOVx], q2);
+  if (hy) q2 = fma2(S2(c.c2_y), od[kOVy], q2);
+  float2 q3 = S2(c.c3_0);
+  if (hx) q3 = fma2(S2(c.c3_xx), S2(vx * vx), q3);
+  if (hx && hy) q3 = fma2(S2(c.c3_xy), S2(vx * vy), q3);
+  if (hx) q3 = fma2(S2(c.c3_x), od[kOVx], q3);
+  if (hy) q3 = fma2(S2(c.c3_y), od[kOVy], q3);
+  if (hx) q3 = fma2(S2(c.c3_xxx), od[kOVx3], q3);
+  if (hx && hy) q3 = fma2(S2(c.c3_xxy), od[kOVx2y], q3);
+  R[0] = fma2(on, S2(c.q0m1), mul2(om, S2(nmT)));
+  R[1] = mul2(on, q1);
+  R[2] = mul2(on, q2);
+  R[3] = mul2(on, q3);
+  if (FORCE) {
+    // lanes (F.v, -F.v) and (F.t, -F.t) times n/T, t = (-vy, vx)
+    float2 Fv, Ft;
+    if (hx && hy) {
+      Fv = fma2(S2(FxT), od[kOVx], mul2(S2(FyT), od[kOVy]));
+      Ft = fma2(S2(FyT), od[kOVx], mul2(S2(FxT), od[kONVy]));
+    } else if (hx) {
+      Fv = mul2(S2(FxT), od[kOVx]);
+      Ft = mul2(S2(FyT), od[kOVx]);
+    } else {
+      Fv = mul2(S2(FyT), od[kOVy]);
+      Ft = mul2(S2(FxT), od[kONVy]);
+    }
+    // minus the shell derivatives dq_m/dtheta on the two lanes
+    float2 nD1;
+    if (hx && hy) nD1 = fma2(S2(c.c1_x), od[kOVy], mul2(S2(c.c1_y), od[kONVx]));
+    else if (hx) nD1 = mul2(S2(c.c1_y), od[kONVx]);
+    else nD1 = mul2(S2(c.c1_x), od[kOVy]);
+    // even part of -dq2/dtheta: 2 vx vy c2_xx + (vy^2 - vx^2) c2_xy
+    float2 nD2 = mul2(S2(c.c2_xy), S2(vy * vy - vx * vx));
+    if (hx && hy) nD2 = fma2(S2(c.c2_xx), S2(2.f * vx * vy), nD2);
+    if (hy) nD2 = fma2(S2(c.c2_x), od[kOVy], nD2);
+    if (hx) nD2 = fma2(S2(c.c2_y), od[kONVx], nD2);
+    float2 nD3 = mul2(S2(c.c3_xy), S2(vy * vy - vx * vx));
+    if (hx && hy) nD3 = fma2(S2(c.c3_xx), S2(2.f * vx * vy), nD3);
+    if (hy) nD3 = fma2(S2(c.c3_x), od[kOVy], nD3);
+    if (hx) nD3 = fma2(S2(c.c3_y), od[kONVx], nD3);
+    if (hx && hy) nD3 = fma2(S2(c.c3_xxx), od[kO3x2y], nD3);
+    if (hx) nD3 = fma2(S2(c.c3_xxy), od[kOX3m2xy2], nD3);
+    const float q0 = 1.f + c.q0m1;
+    // s_m = (F.v)(q_m - (m + 1) q_{m+1}) - (F.t) dq_{m+1}/dtheta
+    R[0] = fma2(Fv, fma2(q1, S2(-1.f), S2(q0)), R[0]);
+    R[0] = fma2(Ft, nD1, R[0]);
+    R[1] = fma2(Fv, fma2(q2, S2(-2.f), q1), R[1]);
+    R[1] = fma2(Ft, nD2, R[1]);
+    R[2] = fma2(Fv, fma2(q3, S2(-3.f), q2), R[2]);
+    R[2] = fma2(Ft, nD3, R[2]);
+    R[3] = fma2(Fv, q3, R[3]);
+  }
+}
+
+// New relative deviations of the four shells of one direction on shell pairs:
+// out_j = (1 - omega) g_j + R0 + R1 p0_j + R2 p0_j^2 + R3 p0_j^3.  With BAL the
+// direction's moment change (sum_j w p0_j (out_j - g_j), sum_j w p0_j^2
+// (out_j - g_j)) is returned in bal (the conservation projection's input).
+template <bool BAL, class C>
+__device__ __forceinline__ void relax_shells_paired(float R0, float R1, float R2, float R3,
+                                                    float omc, int kind, const C& qc, float* f,
+                                                    float2& bal) {
+  const float2 v01 = fma2(fma2(fma2(S2(R3), qc.p01, S2(R2)), qc.p01, S2(R1)), qc.p01, S2(R0));
+  const float2 v23 = fma2(fma2(fma2(S2(R3), qc.p23, S2(R2)), qc.p23, S2(R1)), qc.p23, S2(R0));
+  const float2 i01 = make_float2(f[0], f[1]), i23 = make_float2(f[2], f[3]);
+  const float2 o01 = fma2(S2(omc), i01, v01);
+  const float2 o23 = fma2(S2(omc), i23, v23);
+  if (BAL) {
+    const float2 d01 = fma2(i01, S2(-1.f), o01), d23 = fma2(i23, S2(-1.f), o23);
+    bal = mul2(S2(d01.x), qc.wab[kind][0]);
+    bal = fma2(S2(d01.y), qc.wab[kind][1], bal);
+    bal = fma2(S2(d23.x), qc.wab[kind][2], bal);
+    bal = fma2(S2(d23.y), qc.wab[kind][3], bal);
+  }
+  f[0] = o01.x; f[1] = o01.y; f[2] = o23.x; f[3] = o23.y;
+}
+
+// collide_store() with FP32 arithmetic (FP32 and 16-bit storage) on register
+// pairs: the same quantities in the same order of operations per population,
+// with each instruction serving two directions or two shells.
+template <typename S, int FORCE, int RES, class C>
+__device__ __forceinline__ void collide_store_paired(float (&f)[kQ], S* __restrict__ fout,
+                                                     const DevSample& s, int x, int y,
+                                                     const StepAux<float>& aux, const C& qc,
+                                                     double& r_du2, double& r_u2, uint32_t park,
+                                                     const float* dn_prev, float* dn_next) {
+  constexpr bool kProject = sizeof(S) == sizeof(float);
+  const bool lca = FORCE == kForceLca && s.inv_cg != 0.0;
+  float egx = 0.f, egy = 0.f;
+  if (lca) lca_gradient(s, dn_prev, x, y, egx, egy);
+  const Moments<float> m = moments(f, qc);
+  const uint32_t park_stride = blockDim.x * 16u;
+#pragma unroll
+  for (int d = 0; d < kDirs; ++d) park_store(park + d * park_stride, &f[4 * d]);
+  Macro<float> M;
+  const bool conv = landau(m, M);
+  unsigned bad = 0;
+  if (!conv) bad |= kErrNoConvergence;
+  if (!all_finite(M)) bad |= kErrNonFinite;
+  else if (!macro_ok(M)) bad |= kErrUnphysical;
+  if (bad) atomicOr(aux.err, bad);
+
+  const EqCoeffs<float> c = eq_coeffs(M);
+  const float scl = sizeof(S) == 2 ? qc.enc_s : 1.f;
+  const float inv1T = qdiv(1.f, 1.f + M.dT);
+  const float nT = (1.f + M.dn) * inv1T * scl;
+  const float nmT = (M.dn - M.dT) * inv1T * scl;
+  const float gt = M.gamma * float(s.inv_tau);
+  const float gux = gt * M.ux, guy = gt * M.uy;
+  const float Fx = lca ? float(s.Fx) + (-float(s.inv_cg) * egx) : float(s.Fx);
+  const float Fy = lca ? float(s.Fy) + (-float(s.inv_cg) * egy) : float(s.Fy);
+  const float FxT = Fx * nT, FyT = Fy * nT;
+  const long long site = (long long)y * s.ldx + x;
+  if (lca) dn_next[site] = M.dn;
+  // conservation projection: sums of the moment changes (N^0, T^00) and
+  // (T^0x, T^0y), started with minus the forcing's target
+  float2 accNE = S2(0.f), accXY = S2(0.f);
+  if (kProject && FORCE != 0) {
+    // forcing changes T^0a by (F.N_E, F N_E^0), N_E = n gamma (1, u)
+    const float nG = (1.f + M.dn) * M.gamma;
+    accNE = make_float2(0.f, -(nG * (Fx * M.ux + Fy * M.uy)));
+    accXY = make_float2(-(nG * Fx), -(nG * Fy));
+  }
+  // (5,0)-type pairs first: with FP32 storage they take the correction and
+  // are stored last; the (3,4)-type pairs are stored as soon as done.
+#pragma unroll
+  for (int pi = 0; pi < kDirs / 2; ++pi) {
+    const int d = (2 * pi + 8) % kDirs;
+    const int kind = dir_kind(d);
+    float2 R[4], om;
+    pair_cubics_paired<FORCE != 0>(d, c, nT, nmT, gt, gux, guy, FxT, FyT, qc, R, om);
+    park_load(park + d * park_stride, &f[4 * d]);
+    park_load(park + (d + 1) * park_stride, &f[4 * d + 4]);
+    const float2 omc = fma2(om, S2(-1.f), S2(1.f));
+    float2 bp, bn;
+    relax_shells_paired<kProject>(R[0].x, R[1].x, R[2].x, R[3].x, omc.x, kind, qc, &f[4 * d], bp);
+    relax_shells_paired<kProject>(R[0].y, R[1].y, R[2].y, R[3].y, omc.y, kind, qc, &f[4 * d + 4],
+                                  bn);
+    if (kProject) {
+      accNE = add2(accNE, add2(bp, bn));
+      accXY = fma2(S2(bp.y - bn.y), qc.vxy[d / 2], accXY);
+    }
+    if (!kProject || kind == 0) {
+      Codec<S>::store4(fout + vec_index(s, d, site), kind, qc, &f[4 * d]);
+      Codec<S>::store4(fout + vec_index(s, d + 1, site), kind, qc, &f[4 * d + 4]);
+    } else {
+      // (5,0)-type: wait for the correction in the parking area, not in registers
+      park_store(park + d * park_stride, &f[4 * d]);
+      park_store(park + (d + 1) * park_stride, &f[4 * d + 4]);
+    }
+  }
+  if (kProject) {
+    const float rN = accNE.x, rE = accNE.y;
+    const float l0 = qc.P00 * rN + qc.P01 * rE;
+    const float l1 = qc.P10 * rN + qc.P11 * rE;
+    const float lx = qc.px * accXY.x, ly = qc.px * accXY.y;
+#pragma unroll
+    for (int d = 8; d < kDirs; ++d) {
+      const float cd = l1 + (hop_x(d) > 0 ? lx : hop_x(d) < 0 ? -lx : hop_y(d) > 0 ? ly : -ly);
+      park_load(park + d * park_stride, &f[4 * d]);
+      // delta += w (l0 + p0 cd)
+      const float2 t01 = fma2(S2(cd), qc.p01, S2(l0));
+      const float2 t23 = fma2(S2(cd), qc.p23, S2(l0));
+      const float2 o01 = add2(make_float2(f[4 * d], f[4 * d + 1]), t01);
+      const float2 o23 = add2(make_float2(f[4 * d + 2], f[4 * d + 3]), t23);
+      f[4 * d] = o01.x; f[4 * d + 1] = o01.y; f[4 * d + 2] = o23.x; f[4 * d + 3] = o23.y;
+      Codec<S>::store4(fout + vec_index(s, d, site), 1, qc, &f[4 * d]);
+    }
+  }
+  if (RES == 1) {
+    const long long k = s.site0 + (long long)y * s.nx + x;
+    aux.uprev[2 * k] = M.ux;
+    aux.uprev[2 * k + 1] = M.uy;
+  } else if (RES == 2) {
+    const long long k = s.site0 + (long long)y * s.nx + x;
+    const double dx = double(M.ux) - double(aux.uprev[2 * k]);
+    const double dy = double(M.uy) - double(aux.uprev[2 * k + 1]);
+    r_du2 += dx * dx + dy * dy;
+    r_u2 += double(M.ux) * double(M.ux) + double(M.uy) * double(M.uy);
+  }
+}
+
 // Collision of the gathered deviations f of site (x < nx, y) and store of the
 // 48 new deviations into fout.  RES: 0 nothing extra; 1 store u for the
 // residual; 2 add |u - u_prev|^2 and |u|^2 to r_du2, r_u2 (the caller
@@ -406,6 +622,11 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
                                               const typename Codec<S>::R* dn_prev,
                                               typename Codec<S>::R* dn_next) {
   using R = typename Codec<S>::R;
+  if constexpr (std::is_same<R, float>::value) {
+    collide_store_paired<S, FORCE, RES>(f, fout, s, x, y, aux, qc, r_du2, r_u2, park, dn_prev,
+                                        dn_next);
+    return;
+  }
   // FP32 storage: the FP32 quadrature constants satisfy Eq. orthonormal only
   // to ~1e-7, which would break the exact conservation of N^0 and T^0a by the
   // collision at that level every step (a secular drift).  The update is
@@ -568,6 +789,7 @@ struct BatchArgs {
   int nsamples;
   int cur;
   long long ntiles;
+  long long wait_limit;   // clock cycles a wait for a staged tile may take before it gives up
 };
 
 template <typename S, int FORCE, int RES, int BX, class C>
@@ -611,9 +833,11 @@ __device__ __forceinline__ void batch_body(S* __restrict__ base, const BatchArgs
 // that the last warp to finish gathering tile k (a shared counter per buffer)
 // issues tile k + 2 into the buffer it just freed, so two tiles are always in
 // flight or landed and no warp waits for another one.  Every wait is bounded
-// (about 1 s): a warp that gives up sets kErrTimeout and a shared abort flag,
-// waits once more (bounded) for the copies of both buffers, and leaves the
-// loop; the other warps leave at their next tile.
+// (b.wait_limit cycles, about 1 s by default): a warp that gives up sets
+// kErrTimeout and a shared abort flag, waits once more for the copies of both
+// buffers (bounded by the full ~1 s whatever b.wait_limit is, so that no bulk
+// copy into the block's shared memory is left in flight), and leaves the loop;
+// the other warps leave at their next tile.
 template <typename S, int FORCE, int RES, int BX, class C>
 __device__ __forceinline__ void staged_batch_body(S* __restrict__ base, const BatchArgs& b,
                                                   const typename Codec<S>::R* __restrict__ ghost,
@@ -671,7 +895,7 @@ __device__ __forceinline__ void staged_batch_body(S* __restrict__ base, const Ba
 #pragma unroll 1
   for (int it = 0;; ++it) {
     const int cb = it & 1;
-    bool ok = !*abort_flag && stage_wait(full_bar(cb), (it >> 1) & 1);
+    bool ok = !*abort_flag && stage_wait(full_bar(cb), (it >> 1) & 1, b.wait_limit);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) {
       if (lane == 0 && !*abort_flag) {
@@ -747,16 +971,11 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ fin, const De
   if (dn_out) dn_out[(long long)y * s.ldx + x] = M.dn;
 }
 
-// Stored state := f^eq(n, u, T) - w (dense FP64 inputs).
-template <typename S, class C>
-__device__ __forceinline__ void init_body(S* __restrict__ fout, const DevSample& s,
-                                          const double* n, const double* ux, const double* uy,
-                                          const double* T, unsigned* err, const C& qc) {
-  using R = typename Codec<S>::R;
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y;
-  if (x >= s.nx) return;
-  const long long k = (long long)y * s.nx + x;
+// Macroscopic state of site k of dense FP64 fields (n, u, T).
+template <typename R>
+__device__ __forceinline__ Macro<R> field_macro(const double* n, const double* ux,
+                                                const double* uy, const double* T, long long k,
+                                                bool& ok) {
   Macro<R> M;
   const double vx = ux[k], vy = uy[k];
   const double u2 = vx * vx + vy * vy;
@@ -768,24 +987,109 @@ __device__ __forceinline__ void init_body(S* __restrict__ fout, const DevSample&
   M.dn = R(n[k] - 1.0);
   M.dT = R(T[k] - 1.0);
   M.deps = R(0);
-  if (!(u2 < 1.0) || !(n[k] > 0.0) || !(T[k] > 0.0) || !isfinite(n[k]) || !isfinite(T[k]))
-    atomicOr(err, kErrUnphysical);
-  const EqCoeffs<R> c = eq_coeffs(M);
+  ok = (u2 < 1.0) && (n[k] > 0.0) && (T[k] > 0.0) && isfinite(n[k]) && isfinite(T[k]);
+  return M;
+}
+
+// Relative deviations (f^eq - w) / w of the two directions d (even), d + 1
+// for the macroscopic state M (times s in 16-bit storage): vp, vn.
+template <typename S, class C>
+__device__ __forceinline__ void eq_pair(const Macro<typename Codec<S>::R>& M,
+                                        const EqCoeffs<typename Codec<S>::R>& c, int d,
+                                        const C& qc, typename Codec<S>::R* vp,
+                                        typename Codec<S>::R* vn) {
+  using R = typename Codec<S>::R;
   const R scl = sizeof(S) == 2 ? qc.enc_s : R(1);     // 16-bit storage holds s g
   const R inv1T = R(1) / (R(1) + M.dT);
   const R nT = (R(1) + M.dn) * inv1T * scl;
   const R nmT = (M.dn - M.dT) * inv1T * scl;
+  R Rp[4], Rn[4], omp, omn;
+  // omega = 1 and no force: out = w (f^eq - w) / w
+  pair_cubics<R, false>(d, c, nT, nmT, R(1), R(0), R(0), R(0), R(0), Rp, Rn, omp, omn);
+#pragma unroll
+  for (int j = 0; j < kShells; ++j) vp[j] = vn[j] = R(0);
+  relax_shells(Rp, R(1), dir_kind(d), qc, vp);
+  relax_shells(Rn, R(1), dir_kind(d), qc, vn);
+}
+
+// Stored state := f^eq(n, u, T) - w (dense FP64 inputs).
+template <typename S, class C>
+__device__ __forceinline__ void init_body(S* __restrict__ fout, const DevSample& s,
+                                          const double* n, const double* ux, const double* uy,
+                                          const double* T, unsigned* err, const C& qc) {
+  using R = typename Codec<S>::R;
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= s.nx) return;
+  const long long k = (long long)y * s.nx + x;
+  bool ok;
+  const Macro<R> M = field_macro<R>(n, ux, uy, T, k, ok);
+  if (!ok) atomicOr(err, kErrUnphysical);
+  const EqCoeffs<R> c = eq_coeffs(M);
   const long long site = (long long)y * s.ldx + x;
   void* const dn0 = s.cur ? s.dn[1] : s.dn[0];
   if (dn0) static_cast<R*>(dn0)[site] = M.dn;     // the electric force's first step
 #pragma unroll
   for (int d = 0; d < kDirs; d += 2) {
-    R Rp[4], Rn[4], omp, omn;
-    // omega = 1 and no force: out = w (f^eq - w) / w
-    pair_cubics<R, false>(d, c, nT, nmT, R(1), R(0), R(0), R(0), R(0), Rp, Rn, omp, omn);
-    R v[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-    relax_shells(Rp, R(1), dir_kind(d), qc, v);
-    relax_shells(Rn, R(1), dir_kind(d), qc, v + 4);
+    R v[8];
+    eq_pair<S>(M, c, d, qc, v, v + 4);
+    Codec<S>::store4(fout + vec_index(s, d, site), dir_kind(d), qc, v);
+    Codec<S>::store4(fout + vec_index(s, d + 1, site), dir_kind(d), qc, v + 4);
+  }
+}
+
+// Stored state := the Chapman-Enskog seed of the fields (n, u, T): the state
+// whose first pull-stream gives f^eq plus its first-order non-equilibrium part
+// of a steady flow (steady Eq. discrete-rbe with f - f^eq small and slowly
+// varying),
+//     f_i(x) = f^eq_i(x) - (f^eq_i(x) - f^eq_i(x - n_i)) / omega_i(x),
+// omega_i = gamma (1 - v_i.u) / tau, wherever the source x - n_i lies in the
+// sample.  Stored per source site s with d = s + n_i (wrapped on periodic
+// axes):  f*_i(s) = f^eq_i(d) - (f^eq_i(d) - f^eq_i(s)) / omega_i(d), and
+// f^eq_i(s) where d lies outside (only the bounce-back at s reads it).  The
+// relation is affine with unit weight on f^eq, so it holds for the stored
+// relative deviations as well.  Each thread evaluates the equilibrium at its
+// own site and, for each direction, at the arrival site.
+template <typename S, class C>
+__device__ __forceinline__ void init_ce_body(S* __restrict__ fout, const DevSample& s,
+                                             const double* n, const double* ux,
+                                             const double* uy, const double* T, unsigned* err,
+                                             const C& qc) {
+  using R = typename Codec<S>::R;
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= s.nx) return;
+  const long long k = (long long)y * s.nx + x;
+  bool ok;
+  const Macro<R> M = field_macro<R>(n, ux, uy, T, k, ok);
+  if (!ok) atomicOr(err, kErrUnphysical);
+  const EqCoeffs<R> c = eq_coeffs(M);
+  const long long site = (long long)y * s.ldx + x;
+  void* const dn0 = s.cur ? s.dn[1] : s.dn[0];
+  if (dn0) static_cast<R*>(dn0)[site] = M.dn;     // the electric force's first step
+#pragma unroll 1
+  for (int d = 0; d < kDirs; d += 2) {
+    R v[8];
+    eq_pair<S>(M, c, d, qc, v, v + 4);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int dd = d + h;
+      int tx = x + hop_x(dd), ty = y + hop_y(dd);
+      if (s.periodic_x) tx = tx < 0 ? tx + s.nx : (tx >= s.nx ? tx - s.nx : tx);
+      if (s.periodic_y) ty = ty < 0 ? ty + s.ny : (ty >= s.ny ? ty - s.ny : ty);
+      if ((unsigned)tx < (unsigned)s.nx && (unsigned)ty < (unsigned)s.ny) {
+        bool okd;
+        const Macro<R> Md = field_macro<R>(n, ux, uy, T, (long long)ty * s.nx + tx, okd);
+        R ed[8];
+        eq_pair<S>(Md, eq_coeffs(Md), d, qc, ed, ed + 4);
+        const R vx = R(hop_x(dd)) / R(5), vy = R(hop_y(dd)) / R(5);
+        const R om = Md.gamma * (R(1) - (vx * Md.ux + vy * Md.uy)) * R(s.inv_tau);
+        const R iom = R(1) / om;
+#pragma unroll
+        for (int j = 0; j < kShells; ++j)
+          v[4 * h + j] = ed[4 * h + j] - (ed[4 * h + j] - v[4 * h + j]) * iom;
+      }
+    }
     Codec<S>::store4(fout + vec_index(s, d, site), dir_kind(d), qc, v);
     Codec<S>::store4(fout + vec_index(s, d + 1, site), dir_kind(d), qc, v + 4);
   }

@@ -3,6 +3,6 @@
 #include <cuda_bf16.h>
 #define RLBM_S __nv_bfloat16
 #define RLBM_OPS ops_bf16
-#define RLBM_STEP_MIN_BLOCKS 6
+#define RLBM_STEP_MIN_BLOCKS 7
 #define RLBM_NAME "bf16"
 #include "prec_impl.cuh"

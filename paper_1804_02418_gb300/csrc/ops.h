@@ -30,6 +30,9 @@ struct PrecOps {
                          cudaStream_t st);
   cudaError_t (*init)(void* fout, const DevSample& s, const double* n, const double* ux,
                       const double* uy, const double* T, unsigned* err, cudaStream_t st);
+  // the Chapman-Enskog seed of the fields (kernels.cuh: init_ce_body)
+  cudaError_t (*init_ce)(void* fout, const DevSample& s, const double* n, const double* ux,
+                         const double* uy, const double* T, unsigned* err, cudaStream_t st);
   // planes q0 .. q0+nq-1 <-> dense FP64 [nq][ny][nx]
   cudaError_t (*get_state)(const void* fin, const DevSample& s, int q0, int nq, double* out,
                            cudaStream_t st);

@@ -15,10 +15,10 @@ using R = typename Codec<S>::R;
 __constant__ QuadConsts<R> c_qc;
 
 // RLBM_STEP_MIN_BLOCKS: resident blocks of 128 threads per SM the register
-// allocation aims for (measured per storage type: with the populations parked
-// in shared memory, FP32 arithmetic runs best at 6 blocks / 80 registers, for
-// FP32 and 16-bit storage alike; the FP64 kernels take all the registers
-// they want).
+// allocation aims for (measured per storage type, with the populations parked
+// in shared memory and the paired FP32 collision: FP32 storage runs best at
+// 6 blocks / 80 registers, 16-bit storage at 7 blocks / 72 registers; the
+// FP64 kernels take all the registers they want).
 #ifndef RLBM_STEP_MIN_BLOCKS
 #define RLBM_STEP_MIN_BLOCKS 4
 #endif
@@ -86,6 +86,13 @@ __global__ void __launch_bounds__(kBX) k_init(S* __restrict__ fout, DevSample s,
   init_body<S>(fout, s, n, ux, uy, T, err, c_qc);
 }
 
+__global__ void __launch_bounds__(kBX) k_init_ce(S* __restrict__ fout, DevSample s,
+                                                 const double* n, const double* ux,
+                                                 const double* uy, const double* T,
+                                                 unsigned* err) {
+  init_ce_body<S>(fout, s, n, ux, uy, T, err, c_qc);
+}
+
 __global__ void __launch_bounds__(kBX) k_get(const S* __restrict__ fin, DevSample s, int q0,
                                              double* out) {
   get_state_body<S>(fin, s, q0, out, c_qc);
@@ -113,6 +120,22 @@ cudaError_t upload(const double p0[4], const double w[2][4], double scale) {
     }
     for (int m = 1; m <= 3; ++m) K[m] += w[1][j] * std::pow(p0[j], m);
   }
+  // operand pairs of the paired FP32 arithmetic (the values the kernels use)
+  for (int q = 0; q < kDirs / 2; ++q) {
+    const int d = 2 * q;
+    const double vx = hop_x(d) / 5.0, vy = hop_y(d) / 5.0;
+    for (int o = 0; o < kOddMonos; ++o)
+      h.odd[q][o] = make_float2(float(odd_mono(d, o)), float(-odd_mono(d, o)));
+    h.vxy[q] = make_float2(float(vx), float(vy));
+    h.vsq[q] = make_float2(float(vx * vx), float(vx * vy));
+  }
+  for (int k = 0; k < 2; ++k) {
+    for (int j = 0; j < kShells; ++j)
+      h.wab[k][j] = make_float2(float(w[k][j] * p0[j] / scale),
+                                float(w[k][j] * p0[j] * p0[j] / scale));
+  }
+  h.p01 = make_float2(float(p0[0]), float(p0[1]));
+  h.p23 = make_float2(float(p0[2]), float(p0[3]));
   // Conservation projection on the four (5,0)-type directions:
   //   [4K1 4K2; 4K2 4K3] (l0, l1) = -(rN, rE),   2 K3 lx = -rX,  2 K3 ly = -rY.
   const double det = 16.0 * (K[1] * K[3] - K[2] * K[2]);
@@ -202,6 +225,12 @@ cudaError_t init(void* fout, const DevSample& s, const double* n, const double* 
   return cudaGetLastError();
 }
 
+cudaError_t init_ce(void* fout, const DevSample& s, const double* n, const double* ux,
+                    const double* uy, const double* T, unsigned* err, cudaStream_t st) {
+  k_init_ce<<<site_grid(s), kBX, 0, st>>>(static_cast<S*>(fout), s, n, ux, uy, T, err);
+  return cudaGetLastError();
+}
+
 cudaError_t get_state(const void* fin, const DevSample& s, int q0, int nq, double* out,
                       cudaStream_t st) {
   dim3 grid = site_grid(s);
@@ -219,7 +248,7 @@ cudaError_t set_state(void* fout, const DevSample& s, int q0, int nq, const doub
 }
 
 const PrecOps kOps = {
-    RLBM_NAME, sizeof(S), sizeof(R), upload, step, step_batch, moments, init, get_state,
+    RLBM_NAME, sizeof(S), sizeof(R), upload, step, step_batch, moments, init, init_ce, get_state,
     set_state, 1,
 };
 

@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace rlbm {
 
 constexpr int kQ = 48;
@@ -40,6 +42,22 @@ __host__ __device__ constexpr int hop_y(int d) {
 }
 __host__ __device__ constexpr int dir_kind(int d) { return d < 8 ? 0 : 1; }
 
+// Odd monomials of a unit velocity v whose (a, -a) pairs the paired FP32
+// collision uses (order of QuadConsts::odd).
+enum OddMono {
+  kOVx = 0, kOVy, kONVx, kONVy,   // vx, vy, -vx, -vy
+  kOVx3, kOVx2y,                  // vx^3, vx^2 vy
+  kO3x2y, kOX3m2xy2,              // 3 vx^2 vy, -(vx^3 - 2 vx vy^2)
+  kOddMonos
+};
+
+__host__ __device__ constexpr double odd_mono(int d, int o) {
+  const double vx = hop_x(d) / 5.0, vy = hop_y(d) / 5.0;
+  return o == kOVx ? vx : o == kOVy ? vy : o == kONVx ? -vx : o == kONVy ? -vy
+       : o == kOVx3 ? vx * vx * vx : o == kOVx2y ? vx * vx * vy
+       : o == kO3x2y ? 3.0 * vx * vx * vy : -(vx * vx * vx - 2.0 * vx * vy * vy);
+}
+
 // Quadrature constants (refined Sec. 2.3 values), uploaded once per module.
 template <typename R>
 struct QuadConsts {
@@ -53,6 +71,16 @@ struct QuadConsts {
   // w_2j (l0 + l1 p0_j + p0_j (lx vx + ly vy)) on the (5,0)-type directions,
   // (l0, l1) = P (rN, rE), (lx, ly) = px (rX, rY).
   R P00, P01, P10, P11, px;
+  // Operand pairs of the paired FP32 arithmetic (FP32 kernels only).  Pair
+  // lanes are (direction d, its opposite d + 1) in the collision and (shell
+  // j, shell j + 1) in the relaxation; a constant pair read from here costs
+  // nothing as an operand, a literal pair of two different values would.
+  // odd[q][o]: (a, -a) for the odd monomial o of direction pair q = d / 2.
+  float2 odd[kDirs / 2][kOddMonos];
+  float2 vxy[kDirs / 2];      // (vx, vy) of direction 2q
+  float2 vsq[kDirs / 2];      // (vx^2, vx vy) of direction 2q
+  float2 wab[2][kShells];     // (w p0_j / s, w p0_j^2 / s) by direction kind
+  float2 p01, p23;            // (p0_0, p0_1), (p0_2, p0_3)
 };
 
 // Geometry and physics of one sample as seen by the kernels.
@@ -144,31 +172,25 @@ template <typename H> struct Codec16 {
   using R = float;
   __device__ static float tof(H h);
   __device__ static H fromf(float f);
+  // two stored values <-> two floats (one conversion instruction per pair)
+  __device__ static float2 unpack2(uint32_t u);
+  __device__ static uint32_t pack2(float a, float b);
   template <class C>
   __device__ static void load4(const H* p, int kind, const C& c, R* o) {
     const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-    H h[4];
-    memcpy(h, &u, sizeof u);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]);     // s g: the kernels work scaled
+    const float2 a = unpack2(u.x), b = unpack2(u.y);   // s g: the kernels work scaled
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
   }
   template <class C>
   __device__ static void load4s(uint32_t a, int kind, const C& c, R* o) {
     uint2 u;
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];\n" : "=r"(u.x), "=r"(u.y) : "r"(a));
-    H h[4];
-    memcpy(h, &u, sizeof u);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) o[j] = tof(h[j]);     // s g: the kernels work scaled
+    const float2 x = unpack2(u.x), y = unpack2(u.y);
+    o[0] = x.x; o[1] = x.y; o[2] = y.x; o[3] = y.y;
   }
   template <class C>
   __device__ static void store4(H* p, int kind, const C& c, const R* v) {
-    H h[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) h[j] = fromf(v[j]);
-    uint2 u;
-    memcpy(&u, h, sizeof u);
-    *reinterpret_cast<uint2*>(p) = u;
+    *reinterpret_cast<uint2*>(p) = make_uint2(pack2(v[0], v[1]), pack2(v[2], v[3]));
   }
   // stored s g <-> deviation delta = f - w (state I/O, in FP64: exact round trip)
   template <class C> __device__ static double decode(H v, int kind, int j, const C& c) {
@@ -178,6 +200,28 @@ template <typename H> struct Codec16 {
     return fromf(float(v / c.wd[kind][j] * double(c.enc_s)));
   }
 };
+template <> __device__ inline float2 Codec16<__half>::unpack2(uint32_t u) {
+  __half2 h;
+  memcpy(&h, &u, sizeof u);
+  return __half22float2(h);
+}
+template <> __device__ inline uint32_t Codec16<__half>::pack2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  uint32_t u;
+  memcpy(&u, &h, sizeof u);
+  return u;
+}
+template <> __device__ inline float2 Codec16<__nv_bfloat16>::unpack2(uint32_t u) {
+  __nv_bfloat162 h;
+  memcpy(&h, &u, sizeof u);
+  return __bfloat1622float2(h);
+}
+template <> __device__ inline uint32_t Codec16<__nv_bfloat16>::pack2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  uint32_t u;
+  memcpy(&u, &h, sizeof u);
+  return u;
+}
 template <> __device__ inline float Codec16<__half>::tof(__half h) { return __half2float(h); }
 template <> __device__ inline __half Codec16<__half>::fromf(float f) { return __float2half_rn(f); }
 template <> __device__ inline float Codec16<__nv_bfloat16>::tof(__nv_bfloat16 h) { return __bfloat162float(h); }
@@ -216,7 +260,7 @@ struct Moments {
 };
 
 template <typename R, class C>
-__device__ __forceinline__ Moments<R> moments(const R (&f)[kQ], const C& qc) {
+__device__ __forceinline__ Moments<R> moments_scalar(const R (&f)[kQ], const C& qc) {
   Moments<R> m;
   m.dN0 = m.dNx = m.dNy = m.dE = m.Mx = m.My = m.dPxx = m.dPxy = R(0);
 #pragma unroll
@@ -249,6 +293,65 @@ __device__ __forceinline__ Moments<R> moments(const R (&f)[kQ], const C& qc) {
   }
   m.dPyy = m.dE - m.dPxx;   // massless shells: T^00 = T^xx + T^yy exactly
   return m;
+}
+
+// ---------------------------------------------------------------------------
+// Paired FP32 arithmetic.  Blackwell retires two FP32 fused multiply-adds per
+// instruction on a register pair (the same per-lane rounding as two scalar
+// ones); the FP32 step is bound by its instruction issue, so its collision is
+// written on pairs.  A pair whose lanes hold the same value ("splat") costs
+// nothing extra as an operand.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 S2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// The moments of moments() on pairs: lanes (A_d, B_d) of one direction,
+// A_d = sum_j w p0_j g_dj, B_d = sum_j w p0_j^2 g_dj.
+template <class C>
+__device__ __forceinline__ Moments<float> moments_paired(const float (&f)[kQ], const C& qc) {
+  float2 NE = S2(0.f), NxMx = S2(0.f), NyMy = S2(0.f), PP = S2(0.f);
+#pragma unroll
+  for (int d = 0; d < kDirs; d += 2) {
+    const int k = dir_kind(d);
+    float2 ABp = mul2(S2(f[4 * d]), qc.wab[k][0]);
+    float2 ABn = mul2(S2(f[4 * d + 4]), qc.wab[k][0]);
+#pragma unroll
+    for (int j = 1; j < kShells; ++j) {
+      ABp = fma2(S2(f[4 * d + j]), qc.wab[k][j], ABp);
+      ABn = fma2(S2(f[4 * d + 4 + j]), qc.wab[k][j], ABn);
+    }
+    const float2 e = add2(ABp, ABn);                 // (A_e, B_e): even parts
+    const float2 o = fma2(ABn, S2(-1.f), ABp);       // (A_o, B_o): odd parts
+    const float vx = float(hop_x(d)) / 5.f, vy = float(hop_y(d)) / 5.f;
+    if (d == 0) {
+      NE = e;
+      NxMx = mul2(o, S2(vx));
+      NyMy = mul2(o, S2(vy));
+      PP = mul2(S2(e.y), qc.vsq[d / 2]);
+    } else {
+      NE = add2(NE, e);
+      if (hop_x(d) != 0) NxMx = fma2(o, S2(vx), NxMx);
+      if (hop_y(d) != 0) NyMy = fma2(o, S2(vy), NyMy);
+      if (hop_x(d) != 0) PP = fma2(S2(e.y), qc.vsq[d / 2], PP);
+    }
+  }
+  Moments<float> m;
+  m.dN0 = NE.x; m.dE = NE.y;
+  m.dNx = NxMx.x; m.Mx = NxMx.y;
+  m.dNy = NyMy.x; m.My = NyMy.y;
+  m.dPxx = PP.x; m.dPxy = PP.y;
+  m.dPyy = m.dE - m.dPxx;   // massless shells: T^00 = T^xx + T^yy exactly
+  return m;
+}
+
+// Moment deviations of 48 streamed relative deviations: paired in FP32,
+// scalar in FP64.
+template <typename R, class C>
+__device__ __forceinline__ Moments<R> moments(const R (&f)[kQ], const C& qc) {
+  if constexpr (std::is_same<R, float>::value) return moments_paired(f, qc);
+  else return moments_scalar(f, qc);
 }
 
 // Landau frame eps U^a = T^ab U_b:  u = (Pi + eps I)^-1 M, eps = E - M.u,

@@ -58,6 +58,7 @@ EXPORTS = {
     "rlbm_workspace_size": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_size_t)]),
     "rlbm_create": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_void_p)]),
     "rlbm_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_int]),
+    "rlbm_init_ce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_int]),
     "rlbm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rlbm_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_int]),
     "rlbm_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
@@ -70,10 +71,12 @@ EXPORTS = {
     "rlbm_sample_residuals": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "rlbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "rlbm_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "rlbm_set_launch_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int]),
     "rlbm_velocity_residual_static": (ctypes.c_int, [ctypes.c_void_p] * 4 + [
         ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
+    "rlbm_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -101,6 +104,17 @@ def quadrature():
     if rc:
         raise RlbmError(rc, lib.rlbm_last_error(None).decode())
     return np.array(w1[:]), np.array(w2[:]), np.array(p0[:])
+
+
+def fma_peak(fp64: bool) -> float:
+    """FMA instructions per second the current device retires (FP64 or FP32),
+    measured by the library's probe kernel."""
+    lib = load_library()
+    r = ctypes.c_double()
+    rc = lib.rlbm_fma_peak(int(bool(fp64)), ctypes.byref(r))
+    if rc:
+        raise RlbmError(rc, lib.rlbm_last_error(None).decode())
+    return r.value
 
 
 def _to_c_sample(s: workloads.Sample) -> _Sample:
@@ -206,6 +220,14 @@ class Solver:
         args = [ctypes.c_void_p(p[0]) if p[0] is not None else None for p in ptrs]
         self._check(self.lib.rlbm_init(self.ctx, sample, *args, int(bool(dev))))
 
+    def init_ce(self, sample: int = 0, n=None, ux=None, uy=None, T=None):
+        """The Chapman-Enskog seed of the fields (rlbm_init_ce): f^eq plus its
+        first-order non-equilibrium part after the first streaming."""
+        ptrs = [_ptr(a) for a in (n, ux, uy, T)]
+        dev = any(p[1] for p in ptrs if p[0] is not None)
+        args = [ctypes.c_void_p(p[0]) if p[0] is not None else None for p in ptrs]
+        self._check(self.lib.rlbm_init_ce(self.ctx, sample, *args, int(bool(dev))))
+
     def step(self, nsteps: int, residual: bool = False):
         if residual:
             r = ctypes.c_double()
@@ -257,6 +279,10 @@ class Solver:
         """Pins the launch shape (bx 0: single-sample kernel; 64 / 128 / 256:
         batched, grid blocks (0: one per tile), staged pulls if staged)."""
         self._check(self.lib.rlbm_set_launch_shape(self.ctx, int(bx), int(grid), int(staged)))
+
+    def set_wait_limit(self, cycles: int):
+        """Longest bounded device wait in clock cycles (0: the default, ~1 s)."""
+        self._check(self.lib.rlbm_set_wait_limit(self.ctx, int(cycles)))
 
     @property
     def steps_done(self) -> int:

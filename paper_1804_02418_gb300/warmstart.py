@@ -112,11 +112,11 @@ def ctypes_stream(torch):
 
 
 def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=20, ref=None,
-             states=None, history=None):
+             ce=False, history=None):
     """Runs every sample to residual <= TOL; returns (steps per sample, wall seconds,
     final fields per sample, distances).  init: optional list of (n, ux, uy, T)
-    host arrays; states: optional list of stored states (f_i - w_i, [48][ny][nx])
-    set instead.  ref: optional reference steady fields; then `distances` holds,
+    host arrays, set as f^eq (rlbm_init) or, with ce, as the Chapman-Enskog
+    seed (rlbm_init_ce).  ref: optional reference steady fields; then `distances` holds,
     per check and sample, ||u(t) - u_ref|| / ||u_ref|| (else None).  history:
     optional list that receives the per-sample residuals of every check."""
     import torch
@@ -125,12 +125,11 @@ def converge(samples, prec, init=None, check=100, max_steps=40000, graph_steps=2
     with torch.cuda.stream(stream):
         sv = rlbm.Solver(samples, prec=prec, stream=stream, graph_steps=graph_steps)
         for i in range(len(samples)):
-            if states is not None:
-                sv.set_state(np.ascontiguousarray(states[i], dtype=np.float64), i)
-            elif init is None:
+            if init is None:
                 sv.init(i)
             else:
-                sv.init(i, *[np.ascontiguousarray(a, dtype=np.float64) for a in init[i]])
+                f = [np.ascontiguousarray(a, dtype=np.float64) for a in init[i]]
+                (sv.init_ce if ce else sv.init)(i, *f)
         sv.autotune()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -300,11 +299,6 @@ def evaluate(net, data, batch):
 # ---------------------------------------------------------------------------
 # Residual analytics and the bound on what a macroscopic seed can gain
 # ---------------------------------------------------------------------------
-# direction hops of the 48-population stencil (population 4 d + j)
-HOPS = [(3, 4), (-3, -4), (-3, 4), (3, -4), (4, 3), (-4, -3), (-4, 3), (4, -3),
-        (5, 0), (-5, 0), (0, 5), (0, -5)]
-
-
 def decay_rates(history, check, lo=TOL, hi=100 * TOL):
     """Late-time decay rate lambda (per step) of every sample's residual,
     r(t) ~ C exp(-lambda t), fitted to the checks where lo <= r <= hi (NaN
@@ -325,54 +319,19 @@ def acoustic_rate(s):
     return 0.5 * nu_lattice(s.tau) * (math.pi / s.nx) ** 2
 
 
-def chapman_enskog_state(s, fields, eq_state):
-    """Stored (post-collision) state that streams to f^eq plus its first-order
-    Chapman-Enskog part: post_i(x) = f^eq_i(x + n_i) - (f^eq_i(x + n_i) - f^eq_i(x)) / omega_i(x),
-    omega_i = gamma (1 - v_i.u) / tau; where x + n_i lies outside the sample
-    the equilibrium at x is kept.  eq_state: the stored state of f^eq of the
-    fields (deviations f - w, [48][ny][nx]); half: see bound_seeds."""
-    n, ux, uy, T = fields
-    g = 1.0 / np.sqrt(1.0 - ux * ux - uy * uy)
-    out = np.empty_like(eq_state)
-    ny, nx = ux.shape
-    for d, (hx, hy) in enumerate(HOPS):
-        om = g * (1.0 - (hx * ux + hy * uy) / 5.0) / s.tau
-        for j in range(4):
-            i = 4 * d + j
-            e = eq_state[i]
-            sh = np.array(e)
-            ys = slice(max(0, -hy), ny - max(0, hy))
-            xs = slice(max(0, -hx), nx - max(0, hx))
-            yd = slice(max(0, hy), ny - max(0, -hy))
-            xd = slice(max(0, hx), nx - max(0, -hx))
-            sh[ys, xs] = e[yd, xd]           # f^eq_i(x + n_i) where it exists
-            out[i] = sh - (sh - e) / om
-    return out
-
-
 def bound_seeds(samples, prec="f64", check=25, max_steps=40000):
     """Steps to residual <= TOL from the rest state and from seeds built out
     of the exact steady fields (as f^eq, partly, and with the first-order
     Chapman-Enskog part), plus the late decay rate of the residual against
     the damping of the longest sound mode.  Yields one dict per seed."""
     steps0, _, steady, _ = converge(samples, prec, check=check, max_steps=max_steps)
-    eq_states = []
-    import torch
-    for s, f in zip(samples, steady):
-        with rlbm.Solver(s, prec="f64") as sv:
-            sv.init(0, *[np.ascontiguousarray(a) for a in f])
-            eq_states.append(sv.get_state(0))
-        torch.cuda.synchronize()
     one = lambda f: np.ones_like(f[0])
     seeds = {
         "rest (n = T = 1, u = 0)": dict(init=None),
         "exact steady n, u, T as f^eq": dict(init=steady),
         "exact steady n, u (T = 1)": dict(init=[(f[0], f[1], f[2], one(f)) for f in steady]),
         "exact steady u (n = T = 1)": dict(init=[(one(f), f[1], f[2], one(f)) for f in steady]),
-        "exact fields + first-order Chapman-Enskog part": dict(
-            states=[chapman_enskog_state(s, f, e) for s, f, e in zip(samples, steady, eq_states)]),
-        "same, half the Chapman-Enskog part": dict(
-            states=[0.5 * (e + chapman_enskog_state(s, f, e)) for s, f, e in zip(samples, steady, eq_states)]),
+        "exact fields + first-order Chapman-Enskog part": dict(init=steady, ce=True),
     }
     ac = np.array([acoustic_rate(s) for s in samples])
     for name, kw in seeds.items():
