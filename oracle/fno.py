@@ -14,11 +14,19 @@ complex C x C matrix R_l(kx, ky), inverse real DFT (numpy.fft.irfft2
 conventions: the ky = 0 column counts once and its imaginary part is
 dropped, ky > 0 counts twice, normalisation 1/N^2).
 
-Both the forward map and its adjoint are written here as products with the
-real DFT matrices of that definition (`dft_mats`), so the backward pass is
-the exact transpose; `spectral_conv_fft` restates the forward with
-numpy.fft as the independent definition the matrices are checked against,
-and the gradients are checked against finite differences (tests).
+Both the forward map and its adjoint are written with numpy.fft from that
+definition (no transform matrices):
+    forward   out = irfft2(pad(R (x) trunc(rfft2(h))))
+    adjoint   with g = d loss / d out (real), the gradient with respect to the
+              kept half-spectrum Z of irfft2 is rfft2(g) c_ky / N^2
+              (c_ky = 1 for ky = 0, 2 otherwise); through the mixing
+              dS = conj(R) dU and dR = sum_b conj(S) dU; and the gradient
+              with respect to h of H = rfft2(h) at the kept modes is
+              Re(sum_kept dH exp(+i 2 pi (kx x + ky y) / N)), one term per
+              kept (kx, ky) (an inverse 2-D FFT of the scattered modes).
+The tests pin the forward against a brute-force double sum over sites and
+modes, the adjoint by the identity <S h, g> = <h, S^T g>, and every gradient
+of the network by central finite differences.
 """
 from __future__ import annotations
 
@@ -38,50 +46,39 @@ def kx_list(N, m1):
     return np.concatenate([np.arange(m1), np.arange(N - m1, N)])
 
 
-def dft_mats(N, m1, m2):
-    """Real matrices of the truncated forward / inverse DFT.
-
-    F1 [2 m2, N]:      y -> (re, im) x ky        (exp(-i 2 pi ky y / N))
-    D  [2 KX, 2 N]:    (x, re/im) -> (kx, re/im)  (exp(-i 2 pi kx x / N)), KX = 2 m1
-    Dinv [2 N, 2 KX]:  (kx, re/im) -> (x, re/im)  (exp(+i 2 pi kx x / N))
-    G  [N, 2 m2]:      (re/im, ky) -> y           (c_ky Re(. exp(+i 2 pi ky y / N)) / N^2)
-    Row / column orders: F1 rows reim * m2 + ky; D rows kxi * 2 + reim,
-    columns x * 2 + reim; G columns reim * m2 + ky.
-    """
-    y = np.arange(N)
-    ky = np.arange(m2)
-    th = 2 * np.pi * np.outer(ky, y) / N                         # [m2, N]
-    F1 = np.concatenate([np.cos(th), -np.sin(th)], axis=0)
-    kx = kx_list(N, m1)
-    ph = 2 * np.pi * np.outer(kx, np.arange(N)) / N              # [KX, N]
-    KX = len(kx)
-    D = np.zeros((2 * KX, 2 * N))
-    D[0::2, 0::2] = np.cos(ph)       # re <- re
-    D[0::2, 1::2] = np.sin(ph)       # re <- im
-    D[1::2, 0::2] = -np.sin(ph)      # im <- re
-    D[1::2, 1::2] = np.cos(ph)       # im <- im
-    Dinv = np.zeros((2 * N, 2 * KX))
-    Dinv[0::2, 0::2] = np.cos(ph).T
-    Dinv[0::2, 1::2] = -np.sin(ph).T
-    Dinv[1::2, 0::2] = np.sin(ph).T
-    Dinv[1::2, 1::2] = np.cos(ph).T
-    c = np.where(ky == 0, 1.0, 2.0)
-    G = np.concatenate([(c[:, None] * np.cos(th)).T, (-c[:, None] * np.sin(th)).T], axis=1) / (N * N)
-    return F1, D, Dinv, G
-
-
 def spectral_conv_fft(h, R, m1):
-    """Definition of the spectral convolution with numpy.fft.  h [B, N, N, C],
-    R complex [2 m1, m2, C, C] (kx order of kx_list)."""
+    """The spectral convolution by its definition with numpy.fft.
+    h [B, N, N, C] real, R complex [2 m1, m2, C, C] (kx order of kx_list)."""
+    return spectral_fwd(h, R, m1)[0]
+
+
+def spectral_fwd(h, R, m1):
+    """Forward of the spectral convolution; returns (out, kept spectrum S)."""
     B, N, _, C = h.shape
     m2 = R.shape[1]
-    H = np.fft.rfft2(h, axes=(1, 2))                            # [B, N, N/2+1, C]
     kx = kx_list(N, m1)
-    Ht = H[:, kx][:, :, :m2]                                    # [B, 2 m1, m2, C]
-    U = np.einsum("bxyi,xyio->bxyo", Ht, R)
-    Up = np.zeros_like(H)
-    Up[:, kx, :m2] = U
-    return np.fft.irfft2(Up, s=(N, N), axes=(1, 2))
+    H = np.fft.rfft2(h, axes=(1, 2))                            # [B, N, N/2+1, C]
+    S = H[:, kx][:, :, :m2]                                     # [B, 2 m1, m2, C]
+    U = np.einsum("bxyi,xyio->bxyo", S, R)
+    Z = np.zeros((B, N, N // 2 + 1, C), dtype=complex)
+    Z[:, kx[:, None], np.arange(m2)[None, :]] = U
+    return np.fft.irfft2(Z, s=(N, N), axes=(1, 2)), S
+
+
+def spectral_bwd(g, R, S, m1):
+    """Adjoint of spectral_fwd: gradients (dh, dR) of a real loss with
+    d loss / d out = g, the kept spectrum S of the forward given."""
+    B, N, _, C = g.shape
+    m2 = R.shape[1]
+    kx = kx_list(N, m1)
+    c = np.where(np.arange(m2) == 0, 1.0, 2.0)
+    dU = np.fft.rfft2(g, axes=(1, 2))[:, kx][:, :, :m2] * (c[None, None, :, None] / (N * N))
+    dS = np.einsum("bxyo,xyio->bxyi", dU, np.conj(R))
+    dR = np.einsum("bxyi,bxyo->xyio", np.conj(S), dU)
+    full = np.zeros((B, N, N, C), dtype=complex)
+    full[:, kx[:, None], np.arange(m2)[None, :]] = dS
+    dh = np.real(np.fft.ifft2(full, axes=(1, 2))) * (N * N)
+    return dh, dR
 
 
 class Oracle:
@@ -90,40 +87,14 @@ class Oracle:
 
     def __init__(self, N, m1, m2):
         self.N, self.m1, self.m2 = N, m1, m2
-        self.F1, self.D, self.Dinv, self.G = dft_mats(N, m1, m2)
 
-    # -- spectral convolution as matrix products ---------------------------
+    # -- spectral convolution (numpy.fft, see the module docstring) ---------
     def spec_fwd(self, h, R):
-        B, N, _, C = h.shape
-        m2, KX = self.m2, 2 * self.m1
-        S1 = np.einsum("ky,bxyc->bxkc", self.F1, h)              # [B, x, (reim, ky), C]
-        S1 = S1.reshape(B, N, 2, m2, C).reshape(B, 2 * N, m2 * C)  # rows (x, reim)
-        S2 = np.einsum("rs,bsj->brj", self.D, S1)                # [B, (kx, reim), (ky, C)]
-        S2c = S2.reshape(B, KX, 2, m2, C)
-        Sc = S2c[:, :, 0] + 1j * S2c[:, :, 1]                    # [B, KX, m2, C]
-        Uc = np.einsum("bxyi,xyio->bxyo", Sc, R)
-        U = np.stack([Uc.real, Uc.imag], axis=2).reshape(B, 2 * KX, m2 * C)
-        Wm = np.einsum("sr,brj->bsj", self.Dinv, U)              # [B, (x, reim), (ky, C)]
-        Wm = Wm.reshape(B, N, 2 * m2, C)                         # [B, x, (reim, ky), C]
-        out = np.einsum("yk,bxkc->bxyc", self.G, Wm)
-        return out, (S1, Sc, Wm)
+        out, S = spectral_fwd(h, R, self.m1)
+        return out, S
 
     def spec_bwd(self, dout, R, cache):
-        S1, Sc, Wm = cache
-        B, N, _, C = dout.shape
-        m2, KX = self.m2, 2 * self.m1
-        dWm = np.einsum("yk,bxyc->bxkc", self.G, dout)           # [B, x, (reim, ky), C]
-        dWm = dWm.reshape(B, 2 * N, m2 * C)
-        dU = np.einsum("sr,bsj->brj", self.Dinv, dWm)            # [B, (kx, reim), (ky, C)]
-        dUc4 = dU.reshape(B, KX, 2, m2, C)
-        dUc = dUc4[:, :, 0] + 1j * dUc4[:, :, 1]
-        dSc = np.einsum("bxyo,xyio->bxyi", dUc, np.conj(R))
-        dR = np.einsum("bxyi,bxyo->xyio", np.conj(Sc), dUc)
-        dS2 = np.stack([dSc.real, dSc.imag], axis=2).reshape(B, 2 * KX, m2 * C)
-        dS1 = np.einsum("rs,brj->bsj", self.D, dS2)              # [B, (x, reim), (ky, C)]
-        dS1 = dS1.reshape(B, N, 2 * m2, C)
-        dh = np.einsum("ky,bxkc->bxyc", self.F1, dS1)
-        return dh, dR
+        return spectral_bwd(dout, R, cache, self.m1)
 
     # -- network -------------------------------------------------------------
     def forward(self, p, x):

@@ -1,7 +1,10 @@
 """Pins for the oracle spectral neural operator (CPU).
 
-* the DFT-matrix form of the spectral convolution equals its definition with
-  numpy.fft (rfft2 / truncation / per-mode mixing / irfft2);
+* the spectral convolution equals a brute-force double sum over sites and
+  kept modes (the definition: forward DFT, truncation, per-mode complex
+  mixing, inverse real DFT with the ky = 0 column counted once);
+* its adjoint satisfies <S h, g> = <h, S^T g> and <S h, g> is linear in R
+  with the gradient the adjoint returns;
 * every parameter gradient of the masked loss equals central finite
   differences of the loss.
 """
@@ -20,15 +23,51 @@ def tiny(seed=0, N=12, C=3, Cq=5, L=2, m1=2, m2=3, B=2):
     return fno.Oracle(N, m1, m2), p, x, t, m
 
 
-def test_matrix_spectral_conv_equals_fft_definition():
+def brute_force_spectral_conv(h, R, m1):
+    """out(x, y) = sum over kept (kx, ky) of c_ky Re(U(kx, ky) e^{+i th}) / N^2,
+    U = sum_i S_i R_io, S(kx, ky) = sum_{x', y'} h(x', y') e^{-i th'},
+    th = 2 pi (kx x + ky y) / N, c_ky = 1 for ky = 0 and 2 otherwise."""
+    B, N, _, C = h.shape
+    m2 = R.shape[1]
+    kxs = list(range(m1)) + list(range(N - m1, N))
+    out = np.zeros_like(h)
+    xs = np.arange(N)
+    for a, kx in enumerate(kxs):
+        for ky in range(m2):
+            ph = np.exp(-2j * np.pi * (kx * xs[:, None] + ky * xs[None, :]) / N)   # [x, y]
+            S = np.einsum("bxyi,xy->bi", h, ph)
+            U = S @ R[a, ky]                                                        # [B, C]
+            c = 1.0 if ky == 0 else 2.0
+            out += c * np.real(U[:, None, None, :] * np.conj(ph)[None, :, :, None]) / (N * N)
+    return out
+
+
+def test_spectral_conv_equals_brute_force_definition():
     rng = np.random.default_rng(1)
-    N, C, m1, m2 = 16, 4, 3, 5
-    o = fno.Oracle(N, m1, m2)
+    N, C, m1, m2 = 10, 3, 3, 4
     h = rng.standard_normal((2, N, N, C))
     R = rng.standard_normal((2 * m1, m2, C, C)) + 1j * rng.standard_normal((2 * m1, m2, C, C))
-    a, _ = o.spec_fwd(h, R)
-    b = fno.spectral_conv_fft(h, R, m1)
+    a = fno.spectral_conv_fft(h, R, m1)
+    b = brute_force_spectral_conv(h, R, m1)
     assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+def test_spectral_adjoint_identity():
+    rng = np.random.default_rng(2)
+    N, C, m1, m2, B = 16, 4, 3, 5, 2
+    h = rng.standard_normal((B, N, N, C))
+    g = rng.standard_normal((B, N, N, C))
+    R = rng.standard_normal((2 * m1, m2, C, C)) + 1j * rng.standard_normal((2 * m1, m2, C, C))
+    out, S = fno.spectral_fwd(h, R, m1)
+    dh, dR = fno.spectral_bwd(g, R, S, m1)
+    lhs = (out * g).sum()
+    assert abs(lhs - (h * dh).sum()) < 1e-12 * np.abs(out * g).sum()
+    # <S h, g> is real-linear in R: its derivative along a direction E is
+    # Re(sum conj(dR) E) (gradient convention d/dRe + i d/dIm)
+    E = rng.standard_normal(R.shape) + 1j * rng.standard_normal(R.shape)
+    t = 1e-3
+    lin = ((fno.spectral_fwd(h, R + t * E, m1)[0] * g).sum() - lhs) / t
+    assert abs(lin - np.real(np.sum(np.conj(dR) * E))) < 1e-9 * max(1.0, abs(lin))
 
 
 def test_gradients_match_finite_differences():
