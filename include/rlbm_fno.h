@@ -57,6 +57,15 @@ int rlbm_gemm_bf16_tc(int transA, int transB, int M, int N, int K, float alpha,
                       float beta, float* C, long long ldc, long long strideC,
                       const float* bias, void* D, int epilogue, int batch, void* stream);
 
+/* The same operation as rlbm_gemm_bf16 on FP32 operands, on the FP32 units
+ * (FP32 products and accumulation): A, B and D are f32 (D receives C's value,
+ * or gelu of it with RLBM_EPI_GELU).  The operator's FP32 mode runs on it. */
+int rlbm_gemm_f32(int transA, int transB, int M, int N, int K, float alpha,
+                  const float* A, long long lda, long long strideA,
+                  const float* B, long long ldb, long long strideB,
+                  float beta, float* C, long long ldc, long long strideC,
+                  const float* bias, float* D, int epilogue, int batch, void* stream);
+
 /* Reads (and clears) the timeout flag of rlbm_gemm_bf16_tc on the current
  * device: *flag = 0 if no CTA gave up since the last call.  Synchronous with
  * respect to the device (the read waits for prior work). */

@@ -144,6 +144,95 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
 }
 
 // ---------------------------------------------------------------------------
+// FP32 GEMM on the FP32 units (the operator's FP32 mode, whose results are
+// compared with the FP64 oracle at 1e-5): 64 x 64 block tiles, K slices of 16
+// staged k-major in shared memory, 256 threads with 4 x 4 outputs each.  Same
+// arguments, layouts and epilogues as k_gemm; D is FP32.
+// ---------------------------------------------------------------------------
+constexpr int FBM = 64, FBN = 64, FBK = 16, kF32Threads = 256;
+
+struct GemmArgsF32 {
+  int transA, transB, M, N, K;
+  float alpha, beta;
+  const float* A;
+  long long lda, strideA;
+  const float* B;
+  long long ldb, strideB;
+  float* C;
+  long long ldc, strideC;
+  const float* bias;
+  float* D;
+  int epilogue;
+};
+
+__global__ void __launch_bounds__(kF32Threads) k_gemm_f32(GemmArgsF32 g) {
+  __shared__ float As[FBK][FBM + 4];
+  __shared__ float Bs[FBK][FBN + 4];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * FBM, n0 = blockIdx.x * FBN;
+  const long long b = blockIdx.z;
+  const float* A = g.A + b * g.strideA;
+  const float* B = g.B + b * g.strideB;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < g.K; k0 += FBK) {
+    // consecutive threads read consecutive addresses of the stored layout
+    for (int i = tid; i < FBM * FBK; i += kF32Threads) {
+      int m, k;
+      if (!g.transA) { m = i / FBK; k = i % FBK; } else { k = i / FBM; m = i % FBM; }
+      const int gm = m0 + m, gk = k0 + k;
+      float v = 0.f;
+      if (gm < g.M && gk < g.K) v = g.transA ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
+      As[k][m] = v;
+    }
+    for (int i = tid; i < FBN * FBK; i += kF32Threads) {
+      int n, k;
+      if (!g.transB) { k = i / FBN; n = i % FBN; } else { n = i / FBK; k = i % FBK; }
+      const int gn = n0 + n, gk = k0 + k;
+      float v = 0.f;
+      if (gn < g.N && gk < g.K) v = g.transB ? B[(long long)gn * g.ldb + gk] : B[(long long)gk * g.ldb + gn];
+      Bs[k][n] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < FBK; ++kk) {
+      float a[4], c[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) c[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], c[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float* C = g.C ? g.C + b * g.strideC : nullptr;
+  float* D = g.D ? g.D + b * g.strideC : nullptr;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = m0 + ty * 4 + i, col = n0 + tx * 4 + j;
+      if (row >= g.M || col >= g.N) continue;
+      const long long o = (long long)row * g.ldc + col;
+      float v = g.alpha * acc[i][j];
+      if (g.epilogue == RLBM_EPI_ATOMIC) {
+        atomicAdd(C + o, v);
+        continue;
+      }
+      if (C && g.beta != 0.f) v += g.beta * C[o];
+      if (g.bias) v += g.bias[col];
+      if (C) C[o] = v;
+      if (D) D[o] = g.epilogue == RLBM_EPI_GELU ? gelu(v) : v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Fifth-generation tensor-core GEMM (tcgen05 / TMEM): one CTA of 4 warps per
 // 128 x BN output tile (BN = 32 / 64 / 128 chosen per call), K in slabs of 64.
 //
@@ -694,6 +783,27 @@ int rlbm_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, con
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
   if (grid.y > 65535) return RLBM_EINVAL;
   k_gemm<<<grid, kGemmThreads, 0, static_cast<cudaStream_t>(stream)>>>(g);
+  return status();
+}
+
+int rlbm_gemm_f32(int transA, int transB, int M, int N, int K, float alpha, const float* A,
+                  long long lda, long long strideA, const float* B, long long ldb,
+                  long long strideB, float beta, float* C, long long ldc, long long strideC,
+                  const float* bias, float* D, int epilogue, int batch, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0 || !A || !B) return RLBM_EINVAL;
+  if (!C && !D) return RLBM_EINVAL;
+  if (epilogue == RLBM_EPI_ATOMIC && !C) return RLBM_EINVAL;
+  if (epilogue < 0 || epilogue > 2 || batch > 65535) return RLBM_EINVAL;
+  GemmArgsF32 g;
+  g.transA = transA; g.transB = transB; g.M = M; g.N = N; g.K = K;
+  g.alpha = alpha; g.beta = C ? beta : 0.f;
+  g.A = A; g.lda = lda; g.strideA = strideA;
+  g.B = B; g.ldb = ldb; g.strideB = strideB;
+  g.C = C; g.ldc = ldc; g.strideC = strideC;
+  g.bias = bias; g.D = D; g.epilogue = epilogue;
+  dim3 grid((N + FBN - 1) / FBN, (M + FBM - 1) / FBM, batch);
+  if (grid.y > 65535) return RLBM_EINVAL;
+  k_gemm_f32<<<grid, kF32Threads, 0, static_cast<cudaStream_t>(stream)>>>(g);
   return status();
 }
 

@@ -54,6 +54,7 @@ _FNO_EXPORTS = {
                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
 }
 _FNO_EXPORTS["rlbm_gemm_bf16_tc"] = _FNO_EXPORTS["rlbm_gemm_bf16"]
+_FNO_EXPORTS["rlbm_gemm_f32"] = _FNO_EXPORTS["rlbm_gemm_bf16"]
 rlbm.EXPORTS.update(_FNO_EXPORTS)
 
 
@@ -113,17 +114,28 @@ class FNOConfig:
 
 class FNO:
     """Parameters live in one flat FP32 vector (Adam state alongside) with a
-    BF16 shadow used by the GEMMs."""
+    BF16 shadow used by the GEMMs.
+
+    act = "bf16" (default): weights, activations and DFT matrices in BF16 on
+    the tensor cores (gemm_impl "tc" or "mma"), FP32 accumulation and FP32
+    spectral mixing.  act = "f32": everything in FP32 on the FP32 units
+    (rlbm_gemm_f32), the same sequence of kernels; the "16" buffers are then
+    the FP32 buffers themselves.  Inputs to forward() are of the act type."""
 
     def __init__(self, cfg: FNOConfig, batch: int, seed: int = 0, device="cuda",
-                 gemm_impl: str = "tc"):
+                 gemm_impl: str = "tc", act: str = "bf16"):
         import torch
         self.torch = torch
         self.cfg, self.B = cfg, batch
         self.lib = _lib()
-        if gemm_impl not in GEMM_IMPLS:
+        if act not in ("bf16", "f32"):
+            raise ValueError("act must be 'bf16' or 'f32'")
+        self.act = act
+        if act == "f32":
+            gemm_impl = "f32"
+        elif gemm_impl not in GEMM_IMPLS:
             raise ValueError(f"gemm_impl must be one of {sorted(GEMM_IMPLS)}")
-        self._gemm_fn = getattr(self.lib, GEMM_IMPLS[gemm_impl])
+        self._gemm_fn = getattr(self.lib, "rlbm_gemm_f32" if act == "f32" else GEMM_IMPLS[gemm_impl])
         N, C, Cq, L, m1, m2, cin = cfg.N, cfg.C, cfg.Cq, cfg.L, cfg.m1, cfg.m2, cfg.cin
         KX = 2 * m1
         self.KX = KX
@@ -141,11 +153,12 @@ class FNO:
         self.grad = torch.zeros(off, **f32)
         self.m = torch.zeros(off, **f32)
         self.v = torch.zeros(off, **f32)
-        self.theta16 = torch.zeros(off, dtype=torch.bfloat16, device=device)
+        f32mode = act == "f32"
+        self.theta16 = self.theta if f32mode else torch.zeros(off, dtype=torch.bfloat16, device=device)
         self.t = 0
         self.set_params(self.init_params(np.random.default_rng(seed)))
         F1, D, Dinv, G = dft_mats(N, m1, m2)
-        b16 = dict(dtype=torch.bfloat16, device=device)
+        b16 = dict(dtype=torch.float32 if f32mode else torch.bfloat16, device=device)
         # row-major copies (G is built column by column and is not C-ordered)
         self.F1 = torch.tensor(np.ascontiguousarray(F1), **b16).contiguous()
         self.D = torch.tensor(np.ascontiguousarray(D), **b16).contiguous()
@@ -161,26 +174,26 @@ class FNO:
         self.S1 = [e16(batch * N, 2 * m2, C) for _ in range(L)]
         self.S2 = [e32(batch, 2 * KX, m2 * C) for _ in range(L)]
         self.U = e32(batch, 2 * KX, m2 * C)
-        self.U16 = e16(batch, 2 * KX, m2 * C)
+        self.U16 = self.U if f32mode else e16(batch, 2 * KX, m2 * C)
         self.Wm16 = e16(batch * N, 2 * m2, C)
         self.z1 = e32(rows, Cq)
         self.y116 = e16(rows, Cq)
         self.y = e32(rows, cfg.cout)
         # backward buffers
         self.dy = e32(rows, cfg.cout)
-        self.dy16 = e16(rows, cfg.cout)
+        self.dy16 = self.dy if f32mode else e16(rows, cfg.cout)
         self.dy1 = e32(rows, Cq)
         self.dz1 = e32(rows, Cq)
-        self.dz116 = e16(rows, Cq)
+        self.dz116 = self.dz1 if f32mode else e16(rows, Cq)
         self.dh = e32(rows, C)
         self.dz = e32(rows, C)
-        self.dz16 = e16(rows, C)
+        self.dz16 = self.dz if f32mode else e16(rows, C)
         self.dWm16 = e16(batch * N, 2 * m2, C)
         self.dU = e32(batch, 2 * KX, m2 * C)
         self.dS2 = e32(batch, 2 * KX, m2 * C)
-        self.dS216 = e16(batch, 2 * KX, m2 * C)
+        self.dS216 = self.dS2 if f32mode else e16(batch, 2 * KX, m2 * C)
         self.dS116 = e16(batch * N, 2 * m2, C)
-        self.dh16 = e16(rows, C)
+        self.dh16 = self.dh if f32mode else e16(rows, C)
         self.loss_buf = torch.zeros(4, **f32)
 
     # -- parameters ---------------------------------------------------------
@@ -201,7 +214,9 @@ class FNO:
         for name, (off, shp) in self.offsets.items():
             th[off:off + int(np.prod(shp))] = np.asarray(params[name], dtype=np.float64).reshape(-1)
         self.theta.copy_(self.torch.from_numpy(th))
-        _ok(self.lib.rlbm_fno_to_bf16(_p(self.theta), _p(self.theta16), self.nparam, None), "to_bf16")
+        if self.act == "bf16":
+            _ok(self.lib.rlbm_fno_to_bf16(_p(self.theta), _p(self.theta16), self.nparam, None),
+                "to_bf16")
 
     def get(self, name, which="theta"):
         off, shp = self.offsets[name]
@@ -238,11 +253,16 @@ class FNO:
             self.gemm(A, B, M, N, rem, lda=M, ldb=N, transA=1, C=out, ldc=N, epi=EPI_ATOMIC)
 
     def to16(self, x, y):
+        """The GEMM-operand copy of an FP32 buffer (BF16 rounding; nothing in
+        FP32 mode, where the two are the same buffer)."""
+        if y.data_ptr() == x.data_ptr():
+            return
         _ok(self.lib.rlbm_fno_to_bf16(_p(x), _p(y), x.numel(), self._stream()), "to_bf16")
 
     # -- forward ------------------------------------------------------------
     def forward(self, x16):
-        """x16: bf16 [B N N, cin] (already on the device).  Returns y (f32 [B N N, 4])."""
+        """x16: [B N N, cin] of the act type (already on the device).  Returns
+        y (f32 [B N N, 4])."""
         c = self.cfg
         N, C, Cq, L, m2, KX = c.N, c.C, c.Cq, c.L, c.m2, self.KX
         B, rows = self.B, self.rows
@@ -298,8 +318,9 @@ class FNO:
         # dy1 = dy Q2^T ; dz1 = dy1 * gelu'(z1)
         self.gemm(self.dy16, self.get("Q2", "theta16"), rows, Cq, c.cout, lda=c.cout, ldb=c.cout,
                   transB=1, C=self.dy1)
-        _ok(self.lib.rlbm_fno_gelu_backward(_p(self.z1), _p(self.dy1), _p(self.dz1), _p(self.dz116),
-                                            rows * Cq, st), "gelu_bwd")
+        _ok(self.lib.rlbm_fno_gelu_backward(_p(self.z1), _p(self.dy1), _p(self.dz1),
+                                            self._p16(self.dz116, self.dz1), rows * Cq, st),
+            "gelu_bwd")
         self.gemm_tn_sum(self.h16[L], self.dz116, C, Cq, rows, self.get("Q1", "grad"))
         _ok(self.lib.rlbm_fno_colsum(_p(self.dz1), _p(self.get("bq1", "grad")), rows, Cq, st), "colsum")
         self.gemm(self.dz116, self.get("Q1", "theta16"), rows, C, Cq, lda=Cq, ldb=Cq, transB=1,
@@ -307,7 +328,8 @@ class FNO:
         for l in reversed(range(L)):
             if l < L - 1:
                 _ok(self.lib.rlbm_fno_gelu_backward(_p(self.z[l]), _p(self.dh), _p(self.dz),
-                                                    _p(self.dz16), rows * C, st), "gelu_bwd")
+                                                    self._p16(self.dz16, self.dz), rows * C, st),
+                    "gelu_bwd")
             else:
                 self.dz.copy_(self.dh)
                 self.to16(self.dz, self.dz16)
@@ -334,8 +356,12 @@ class FNO:
         _ok(self.lib.rlbm_fno_colsum(_p(self.dh), _p(self.get("bp", "grad")), rows, C, st), "colsum")
         return self.grad
 
+    def _p16(self, y16, y32):
+        """Pointer of a kernel's optional BF16 copy output (NULL in FP32 mode)."""
+        return None if y16.data_ptr() == y32.data_ptr() else _p(y16)
+
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         self.t += 1
         _ok(self.lib.rlbm_fno_adam(_p(self.theta), _p(self.grad), _p(self.m), _p(self.v),
-                                   _p(self.theta16), self.nparam, lr, beta1, beta2, eps, self.t,
-                                   self._stream()), "adam")
+                                   self._p16(self.theta16, self.theta), self.nparam, lr, beta1,
+                                   beta2, eps, self.t, self._stream()), "adam")
