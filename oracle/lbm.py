@@ -106,12 +106,22 @@ def tables() -> Tables:
 # Local (per-site) operations; fields have any trailing shape.
 # ---------------------------------------------------------------------------
 
+def _contract(M, v):
+    """sum_i M[..., i] v[i, ...]: a per-site sum over the last index of the
+    constant table M (numpy.einsum without contraction-path optimisation).
+    Unlike a BLAS matrix product, whose blocking may depend on the number of
+    sites, it gives every site the same result whatever the shape of the
+    array the site sits in (the slab-decomposition test relies on that)."""
+    lead = "abcdefgh"[:M.ndim - 1]
+    return np.einsum(f"{lead}i,i...->{lead}...", M, v, optimize=False)
+
+
 def moments(delta):
     """Deviations of N^a and T^ab from their rest values: (dN [3,...], dT [3,3,...])."""
     t = tables()
-    dN = np.tensordot(t.P, delta, axes=(1, 0))
+    dN = _contract(t.P, delta)
     PP = t.P[:, None, :] * t.P[None, :, :]
-    dT = np.tensordot(PP, delta, axes=(2, 0))
+    dT = _contract(PP, delta)
     return dN, dT
 
 
@@ -172,7 +182,7 @@ def equilibrium_deviation(n, ux, uy, T, dn=None, dT=None):
     if dT is None:
         dT = T - 1.0
     a = np.array(expansion.projections_near_rest(ux, uy, dT))       # [16, ...]
-    Qm1 = np.tensordot(t.J[1:].T, a[1:], axes=(1, 0))              # sum_{k>=1} a_k J_k(p_i)
+    Qm1 = _contract(t.J[1:].T, a[1:])                              # sum_{k>=1} a_k J_k(p_i)
     nT = (1.0 + dn) / (1.0 + dT)
     return t.w.reshape((-1,) + (1,) * np.ndim(dn)) * (nT * Qm1 + (dn - dT) / (1.0 + dT))
 
@@ -181,7 +191,7 @@ def equilibrium(n, ux, uy, T):
     """Full f^eq_i = w_i (n/T) sum_k a^(k) J^(k)(p_i) (Eq. feq-expansion-discrete)."""
     t = tables()
     a = np.array(expansion.projections(ux, uy, T))
-    Qf = np.tensordot(t.J.T, a, axes=(1, 0))
+    Qf = _contract(t.J.T, a)
     return t.w.reshape((-1,) + (1,) * np.ndim(n)) * (n / T) * Qf
 
 
@@ -190,10 +200,10 @@ def forcing(n, ux, uy, T, Fx, Fy):
     t = tables()
     a = np.array(expansion.projections(ux, uy, T))
     ex = (1,) * np.ndim(n)
-    Q = np.tensordot(t.J.T, a, axes=(1, 0))
-    dQ0 = np.tensordot(t.dJ[0].T, a, axes=(1, 0))
-    dQx = np.tensordot(t.dJ[1].T, a, axes=(1, 0))
-    dQy = np.tensordot(t.dJ[2].T, a, axes=(1, 0))
+    Q = _contract(t.J.T, a)
+    dQ0 = _contract(t.dJ[0].T, a)
+    dQx = _contract(t.dJ[1].T, a)
+    dQy = _contract(t.dJ[2].T, a)
     Fv = Fx * t.v[0].reshape((-1,) + ex) + Fy * t.v[1].reshape((-1,) + ex)
     return t.w.reshape((-1,) + ex) * (n / T) * (Fv * (Q - dQ0) - (Fx * dQx + Fy * dQy))
 
