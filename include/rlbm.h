@@ -218,6 +218,20 @@ int rlbm_moments(rlbm_ctx* ctx, int sample, double* n, double* ux, double* uy,
 int rlbm_get_state(rlbm_ctx* ctx, int sample, double* delta, int device_ptrs);
 int rlbm_set_state(rlbm_ctx* ctx, int sample, const double* delta, int device_ptrs);
 
+/* Raw stored values of rows y0 .. y0 + nrows - 1 of `sample`'s current state,
+ * for exchanging the halo rows of a domain cut into slabs of rows (one
+ * context per slab; halo rows hold a neighbour's rows).  The buffer `dev`
+ * (device memory of the context's device, caller-owned) holds 12 direction
+ * planes one after another, each nrows x ldx sites x 4 shells in the storage
+ * type (ldx = nx rounded up to a multiple of 32); its size is
+ * rlbm_rows_raw_bytes(ctx, sample, nrows).  A get from one context and a set
+ * into another context of the same precision and nx moves the values bit for
+ * bit.  Asynchronous on the context's stream; RLBM_EINVAL for rows outside
+ * the sample.  (No counterpart in the paper: domain decomposition.) */
+int rlbm_rows_raw_bytes(const rlbm_ctx* ctx, int sample, int nrows, size_t* bytes);
+int rlbm_get_rows_raw(rlbm_ctx* ctx, int sample, int y0, int nrows, void* dev);
+int rlbm_set_rows_raw(rlbm_ctx* ctx, int sample, int y0, int nrows, const void* dev);
+
 /* Synchronises the stream and returns RLBM_ENAN if any kernel since the last
  * check flagged a non-finite or unphysical site (then clears the flag). */
 int rlbm_check(rlbm_ctx* ctx);

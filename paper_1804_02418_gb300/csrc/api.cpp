@@ -915,6 +915,47 @@ int rlbm_moments(rlbm_ctx* c, int sample, double* n, double* ux, double* uy, dou
   return RLBM_OK;
 }
 
+namespace {
+
+// Raw rows [y0, y0 + nrows) of the current state of `sample`: 12 direction
+// planes, each a contiguous run of nrows x ldx sites x 4 shells.
+int rows_raw(rlbm_ctx* c, int sample, int y0, int nrows, void* dev, bool get) {
+  int r = check_sample_index(c, sample);
+  if (r) return r;
+  if (!dev) return fail(c, RLBM_EINVAL, "buffer is NULL");
+  SampleLayout& L = c->samples[sample];
+  if (y0 < 0 || nrows < 1 || y0 + nrows > L.desc.ny)
+    return fail(c, RLBM_EINVAL, "rows %d .. %d outside 0 .. %d", y0, y0 + nrows - 1, L.desc.ny - 1);
+  const size_t eb = c->ops->elem_bytes;
+  const size_t chunk = (size_t)nrows * L.dev.ldx * 4 * eb;       // one plane's rows
+  const size_t pitch = (size_t)L.dev.plane * 4 * eb;            // between planes
+  unsigned char* base = static_cast<unsigned char*>(buf(c, sample, c->cur)) +
+                        (size_t)y0 * L.dev.ldx * 4 * eb;
+  cudaError_t e = get ? cudaMemcpy2DAsync(dev, chunk, base, pitch, chunk, kDirs,
+                                          cudaMemcpyDeviceToDevice, c->stream)
+                      : cudaMemcpy2DAsync(base, pitch, dev, chunk, chunk, kDirs,
+                                          cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "row copy");
+  return RLBM_OK;
+}
+
+}  // namespace
+
+int rlbm_rows_raw_bytes(const rlbm_ctx* c, int sample, int nrows, size_t* bytes) {
+  if (!c || !bytes || sample < 0 || sample >= (int)c->samples.size() || nrows < 0)
+    return RLBM_EINVAL;
+  *bytes = (size_t)kDirs * nrows * c->samples[sample].dev.ldx * 4 * c->ops->elem_bytes;
+  return RLBM_OK;
+}
+
+int rlbm_get_rows_raw(rlbm_ctx* c, int sample, int y0, int nrows, void* dev) {
+  return rows_raw(c, sample, y0, nrows, dev, true);
+}
+
+int rlbm_set_rows_raw(rlbm_ctx* c, int sample, int y0, int nrows, const void* dev) {
+  return rows_raw(c, sample, y0, nrows, const_cast<void*>(dev), false);
+}
+
 int rlbm_get_state(rlbm_ctx* c, int sample, double* delta, int device_ptrs) {
   int r = check_sample_index(c, sample);
   if (r) return r;

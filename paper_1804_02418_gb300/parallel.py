@@ -177,3 +177,61 @@ def run_slab(slab: Slab, state, nsteps: int, step: Callable, group=None):
         state = step(state)
         slab.exchange(state, group)
     return state
+
+
+def exchange_device(slab: Slab, solver, group=None):
+    """Halo exchange of a slab stepped on the GPU by the library (solver: an
+    rlbm.Solver of slab.local, one sample): the slab's own boundary rows are
+    read raw from the device state (rlbm_get_rows_raw), sent to the
+    neighbours and received from them with point-to-point operations of
+    torch.distributed (NCCL), and written raw into the halo rows
+    (rlbm_set_rows_raw): the values move bit for bit.  Messages are ordered as
+    in Slab.exchange.  The solver's stream is synchronised around the
+    exchange."""
+    import torch
+    import torch.distributed as dist
+    nb = solver.rows_raw_bytes(HALO)
+    mk = lambda: torch.empty(nb, dtype=torch.uint8, device="cuda")
+    own_lo, own_hi = slab.lo, slab.lo + slab.own
+    ops, fills = [], []
+    if slab.down is not None:
+        ops.append(dist.P2POp(dist.isend, solver.get_rows_raw(own_lo, HALO, mk()), slab.down,
+                              group, tag=0))
+    if slab.up is not None:
+        ops.append(dist.P2POp(dist.isend, solver.get_rows_raw(own_hi - HALO, HALO, mk()), slab.up,
+                              group, tag=1))
+    if slab.up is not None:
+        b = mk()
+        ops.append(dist.P2POp(dist.irecv, b, slab.up, group, tag=0))
+        fills.append((own_hi, b))
+    if slab.down is not None:
+        b = mk()
+        ops.append(dist.P2POp(dist.irecv, b, slab.down, group, tag=1))
+        fills.append((0, b))
+    torch.cuda.synchronize()
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    torch.cuda.synchronize()
+    for y, b in fills:
+        solver.set_rows_raw(y, HALO, b)
+
+
+def exchange_in_process(slabs: Sequence[Slab], solvers):
+    """The same exchange for slabs stepped by one process on one GPU (one
+    context per slab): device copies between the contexts' states."""
+    import torch
+    torch.cuda.synchronize()
+    for sl, sv in zip(slabs, solvers):
+        nb = sv.rows_raw_bytes(HALO)
+        if sl.down is not None:      # my own bottom rows -> the down neighbour's top halo
+            b = sv.get_rows_raw(sl.lo, HALO, torch.empty(nb, dtype=torch.uint8, device="cuda"))
+            torch.cuda.synchronize()
+            dn = slabs[sl.down]
+            solvers[sl.down].set_rows_raw(dn.lo + dn.own, HALO, b)
+        if sl.up is not None:        # my own top rows -> the up neighbour's bottom halo
+            b = sv.get_rows_raw(sl.lo + sl.own - HALO, HALO,
+                                torch.empty(nb, dtype=torch.uint8, device="cuda"))
+            torch.cuda.synchronize()
+            solvers[sl.up].set_rows_raw(0, HALO, b)
+    torch.cuda.synchronize()

@@ -72,6 +72,12 @@ EXPORTS = {
     "rlbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "rlbm_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
+    "rlbm_rows_raw_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_size_t)]),
+    "rlbm_get_rows_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p]),
+    "rlbm_set_rows_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p]),
     "rlbm_set_launch_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int]),
     "rlbm_velocity_residual_static": (ctypes.c_int, [ctypes.c_void_p] * 4 + [
@@ -279,6 +285,26 @@ class Solver:
         """Pins the launch shape (bx 0: single-sample kernel; 64 / 128 / 256:
         batched, grid blocks (0: one per tile), staged pulls if staged)."""
         self._check(self.lib.rlbm_set_launch_shape(self.ctx, int(bx), int(grid), int(staged)))
+
+    def rows_raw_bytes(self, nrows: int, sample: int = 0) -> int:
+        n = ctypes.c_size_t()
+        self._check(self.lib.rlbm_rows_raw_bytes(self.ctx, sample, int(nrows), ctypes.byref(n)))
+        return n.value
+
+    def get_rows_raw(self, y0: int, nrows: int, out, sample: int = 0):
+        """Raw stored values of rows y0 .. y0 + nrows - 1 into the device
+        tensor `out` (rows_raw_bytes(nrows) bytes)."""
+        if not out.is_cuda or out.numel() * out.element_size() < self.rows_raw_bytes(nrows, sample):
+            raise ValueError("out: a device tensor of rows_raw_bytes(nrows) bytes")
+        self._check(self.lib.rlbm_get_rows_raw(self.ctx, sample, int(y0), int(nrows),
+                                               ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def set_rows_raw(self, y0: int, nrows: int, src, sample: int = 0):
+        if not src.is_cuda or src.numel() * src.element_size() < self.rows_raw_bytes(nrows, sample):
+            raise ValueError("src: a device tensor of rows_raw_bytes(nrows) bytes")
+        self._check(self.lib.rlbm_set_rows_raw(self.ctx, sample, int(y0), int(nrows),
+                                               ctypes.c_void_p(src.data_ptr())))
 
     def set_wait_limit(self, cycles: int):
         """Longest bounded device wait in clock cycles (0: the default, ~1 s)."""

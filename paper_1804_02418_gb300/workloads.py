@@ -129,6 +129,11 @@ def ensemble(count: int = 256, seed0: int = 1234, w_lo: int = 128, w_hi: int = 1
         cw = int(rng.integers(8, 65))
         F = float(10.0 ** rng.uniform(-7.0, -5.0))
         spacing = max(cw + 2 * HOP_RADIUS, L // 4)
+        # narrow samples with wide contacts: move the contacts closer until
+        # both lie on the edge (the contacts of every other sample are as drawn)
+        while spacing > cw and (L // 2 - spacing // 2 - cw // 2 < 0 or
+                                L // 2 + spacing // 2 - cw // 2 + cw > L):
+            spacing -= 1
         s = graphene_sample(nx=L, ny=W, contact_width=cw, contact_spacing=spacing,
                             force=F, tau=tau)
         out.append(s)
