@@ -54,6 +54,29 @@ k_step_staged(S* __restrict__ base, BatchArgs b, const R* __restrict__ ghost, St
   staged_batch_body<S, FORCE, RES, BX>(base, b, ghost, aux, c_qc, stage_smem);
 }
 
+// Shared-memory opt-in of the direct batched kernels: the parking area of a
+// 256-thread block (12 x 256 x 16 B = 48 KiB with FP32 arithmetic) plus the
+// residual reduction's static scratch exceed the default 48 KiB.
+template <int BX>
+cudaError_t allow_park_smem() {
+  const int bytes = (int)park_bytes<R>(BX);
+  cudaError_t e = cudaSuccess;
+  if (bytes == 0) return e;
+  auto set = [&](const void* fn) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  set((const void*)k_step_batch<0, 0, BX>);
+  set((const void*)k_step_batch<0, 1, BX>);
+  set((const void*)k_step_batch<0, 2, BX>);
+  set((const void*)k_step_batch<1, 0, BX>);
+  set((const void*)k_step_batch<1, 1, BX>);
+  set((const void*)k_step_batch<1, 2, BX>);
+  set((const void*)k_step_batch<2, 0, BX>);
+  set((const void*)k_step_batch<2, 1, BX>);
+  set((const void*)k_step_batch<2, 2, BX>);
+  return e;
+}
+
 template <int BX>
 cudaError_t allow_stage_smem() {
   const int bytes = (int)Stage<S>::template smem_bytes<BX>();
@@ -149,6 +172,7 @@ cudaError_t upload(const double p0[4], const double w[2][4], double scale) {
   if (e == cudaSuccess) e = allow_stage_smem<64>();
   if (e == cudaSuccess) e = allow_stage_smem<128>();
   if (e == cudaSuccess) e = allow_stage_smem<256>();
+  if (e == cudaSuccess) e = allow_park_smem<256>();
   return e;
 }
 

@@ -186,6 +186,28 @@ def test_per_sample_residuals(rl, shape):
     assert min(per) <= total <= max(per)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16dev"])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda v: "x".join(map(str, v)))
+def test_residual_steps_in_every_launch_shape(rl, prec, shape):
+    """The residual-reducing launches (static reduction scratch beside the
+    parking area: 48 KiB + 512 B with 256-site blocks) run in every shape and
+    give each sample's residual of a run alone."""
+    samples = uneven_batch()
+    with rl.Solver(samples, prec=prec) as sv:
+        for i, s in enumerate(samples):
+            sv.init(i, *fields(s, 100 + i))
+        sv.set_launch_shape(*shape)
+        sv.step(12, residual=True)
+        per = sv.sample_residuals()
+    alone = []
+    for i, s in enumerate(samples):
+        with rl.Solver(s, prec=prec) as sv:
+            sv.init(0, *fields(s, 100 + i))
+            alone.append(sv.step(12, residual=True))
+    tol = 1e-12 if prec == "f32" else 1e-2
+    assert np.allclose(per, alone, rtol=tol), (per, alone)
+
+
 def test_autotune_cache_round_trip(rl, tmp_path):
     samples = uneven_batch()[:3]
     import json
