@@ -442,9 +442,69 @@ __device__ __forceinline__ ForceSite<R> force_site(const MMacro<R>& M, R Fx, R F
 // ---------------------------------------------------------------------------
 // Collision of one site and store.
 // ---------------------------------------------------------------------------
+// Sign pairs of the paired FP32 arithmetic below (constant memory, so that
+// they cost nothing as operands): (1, -1) and (-1, 1).
+__constant__ float2 c_pm = {1.f, -1.f};
+__constant__ float2 c_mp = {-1.f, 1.f};
+
+__device__ __forceinline__ float2 S2(float a) { return make_float2(a, a); }
+
+// mcollide_store for FP32 on register pairs (lanes: population 2p and its
+// opposite 2p + 1): the same quantities in the same order of operations per
+// population, two populations per paired FMA (Blackwell's FFMA2).
+template <bool FORCE>
+__device__ __forceinline__ void mcollide_store_paired(const float (&g)[kQm], const MMacro<float>& M,
+                                                      float inv_tau, float Fx, float Fy,
+                                                      float* __restrict__ out, long long plane) {
+  const MConsts<float>& c = mc<float>();
+  const EqSite<float> e = eq_site(M);
+  const float gt = M.gamma * inv_tau;
+  const float gux = gt * M.ux, guy = gt * M.uy;
+  ForceSite<float> fs;
+  if (FORCE) fs = force_site(M, Fx, Fy);
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    float ev, od;
+    eq_pair(e, p, ev, od);
+    float wv = 0.f;
+    if (pair_x(p) != 0) wv = gux * c.vx[p];
+    if (pair_y(p) != 0) wv = fmaf(guy, c.vy[p], wv);
+    const float2 om = __ffma2_rn(S2(wv), c_mp, S2(gt));       // gamma (1 -+ v.u) / tau
+    const float2 gpn = __ffma2_rn(S2(od), c_pm, S2(ev));      // (ev + od, ev - od)
+    const float2 G = make_float2(g[2 * p], g[2 * p + 1]);
+    float2 o = __ffma2_rn(om, __ffma2_rn(G, S2(-1.f), gpn), G);
+    if (FORCE) {
+      const float px2 = c.mvE[p][2], pxy = c.mvE[p][3], py2 = c.mvE[p][4], p0 = c.mvE[p][1];
+      const float pxv = c.mvO[p][0], pyv = c.mvO[p][1];
+      float Ae = fmaf(fs.a5, px2, fs.a1), Ao = 0.f, He = fmaf(fs.hp0, p0, fs.h1), Ho = 0.f;
+      Ae = fmaf(fs.a6, pxy, fmaf(fs.a7, py2, Ae));
+      He = fmaf(fs.hxx, px2, fmaf(fs.hxy, pxy, fmaf(fs.hyy, py2, He)));
+      if (pair_x(p) != 0) { Ao = fs.a10 * pxv; Ho = fmaf(fmaf(fs.h0x, p0, fs.hx), pxv, Ho); }
+      if (pair_y(p) != 0) { Ao = fmaf(fs.a11, pyv, Ao); Ho = fmaf(fmaf(fs.h0y, p0, fs.hy), pyv, Ho); }
+      float Fv = 0.f;
+      if (pair_x(p) != 0) Fv = Fx * c.vx[p];
+      if (pair_y(p) != 0) Fv = fmaf(Fy, c.vy[p], Fv);
+      // lanes: +-Fv (1 + g^eq -/+ ... - Ae -+ Ao) - He -+ Ho
+      const float2 X = __ffma2_rn(S2(Ao), c_mp, __fadd2_rn(gpn, S2(1.f - Ae)));
+      o = __ffma2_rn(S2(Fv), __fmul2_rn(X, c_pm), o);
+      o = __ffma2_rn(S2(Ho), c_mp, __fadd2_rn(o, S2(-He)));
+    }
+    out[(long long)(2 * p) * plane] = o.x;
+    out[(long long)(2 * p + 1) * plane] = o.y;
+  }
+  const float gr = eq_rest(e);
+  float orr = fmaf(gt, gr - g[kRestPop], g[kRestPop]);
+  if (FORCE) orr -= fmaf(fs.hp0, float(kM), fs.h1);
+  out[(long long)kRestPop * plane] = orr;
+}
+
 template <typename R, bool FORCE>
 __device__ __forceinline__ void mcollide_store(const R (&g)[kQm], const MMacro<R>& M, R inv_tau,
                                                R Fx, R Fy, R* __restrict__ out, long long plane) {
+  if constexpr (sizeof(R) == sizeof(float)) {
+    mcollide_store_paired<FORCE>(g, M, inv_tau, Fx, Fy, out, plane);
+    return;
+  }
   const MConsts<R>& c = mc<R>();
   const EqSite<R> e = eq_site(M);
   const R gt = M.gamma * inv_tau;
