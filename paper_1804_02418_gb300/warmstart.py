@@ -460,20 +460,20 @@ def converge_grouped(samples, prec, tol, group=48, check=200, max_steps=20000):
     return steps, wall, fields
 
 
-def evaluate_config5(net, held, cfg_N, chan, log, fp64_subset, max32=20000, max64=40000):
-    """Steps and wall time to residual <= 1e-6 of every held-out sample, each
-    run alone (its own context, so that a slow sample holds up no other), from
-    rest and from the operator's seed (its n, u as f^eq, and the same fields
-    as the Chapman-Enskog seed): plain FP64 on the first `fp64_subset`
-    samples, the FP32-then-FP64 route on all of them.  Per sample and arm the
-    JSON line lists steps and seconds; the wall time of a seeded arm includes
-    the operator's inference for that sample."""
+def evaluate_config5(net, held, cfg_N, chan, log, n_eval, max32=20000, max64=40000):
+    """Steps and wall time to residual <= 1e-6 of the first `n_eval` held-out
+    samples, each run alone (its own context, so that a slow sample holds up
+    no other), from rest and from the operator's seed (its n, u as f^eq, and
+    the same fields as the Chapman-Enskog seed), in plain FP64 and through the
+    FP32-then-FP64 route.  Per arm the JSON line lists every sample's steps
+    and seconds; the wall time of a seeded arm includes the operator's
+    inference for that sample."""
     import torch
     arms = [("rest", None, False), ("operator n, u as f^eq", "eq", False),
             ("operator n, u + Chapman-Enskog part", "eq", True)]
     pred = predict_fields(net, held[:1], cfg_N, use=("n", "u"), chan=chan)     # warm-up
     per = {}
-    for route, subset in (("f64", held[:fp64_subset]), ("f32>f64", held)):
+    for route, subset in (("f64", held[:n_eval]), ("f32>f64", held[:n_eval])):
         for name, kind, ce in arms:
             rec = []
             for s in subset:
@@ -499,6 +499,8 @@ def evaluate_config5(net, held, cfg_N, chan, log, fp64_subset, max32=20000, max6
                 line.update(steps_f32_mean=float(r[:, 0].mean()),
                             steps_f32_median=float(np.median(r[:, 0])),
                             f32_cap_hits=int((r[:, 0] >= max32).sum()))
+            line["per_sample_steps_f32_f64_seconds"] = [[int(a), int(b), round(float(c), 4)]
+                                                        for a, b, c, _, _ in rec]
             per[(route, name)] = r
             log(json.dumps(line))
     # per-sample comparisons against plain FP64 from rest on the FP64 subset
@@ -548,7 +550,7 @@ def main_config5(args, log):
                     "u_rel_l2_error_median": float(np.median(err)),
                     "u_rel_l2_error_p90": float(np.percentile(err, 90))}))
     del data, tr, te
-    evaluate_config5(net, held, cfg.N, chan, log, args.fp64_subset)
+    evaluate_config5(net, held, cfg.N, chan, log, args.eval_samples)
 
 
 def main():
@@ -569,7 +571,6 @@ def main():
                     help="config-4-style samples (short side 128-256), grouped runs, evaluation "
                          "of plain FP64 and of the FP32-then-FP64 route from rest and from the seeds")
     ap.add_argument("--group", type=int, default=48)
-    ap.add_argument("--fp64-subset", type=int, default=32)
     args = ap.parse_args()
     log = lambda m: print(m, flush=True)
     if args.config5:
