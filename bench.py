@@ -90,6 +90,7 @@ KERNEL_SOURCES = {
     "bf16dev": ["kernels.cuh", "site.cuh", "prec_impl.cuh", "ops.h", "kernels_bf16.cu"],
     "massive_f32": ["massive.cu", "massive_tables.h", "massive_quadrature.cpp", "dd.h"],
     "massive_f64": ["massive.cu", "massive_tables.h", "massive_quadrature.cpp", "dd.h"],
+    "massive_f32_force0": ["massive.cu", "massive_tables.h", "massive_quadrature.cpp", "dd.h"],
 }
 
 
@@ -105,7 +106,8 @@ def source_hash(key="f32"):
 
 def ncu_traffic(prec):
     """DRAM bytes per launch of the step kernel from the committed ncu summary
-    (key: the precision, or "massive_<precision>"), or None when the kernel
+    (key: the precision, "massive_<precision>", or "massive_f32_force0" for the
+    massive kernel without the force), or None when the kernel
     sources changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(p):
@@ -705,7 +707,7 @@ def massive_arm(args, rank, world, cpu_line):
                          "buffer read (cold L2, no pending write-backs); steps timed alone",
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": ncu_traffic("massive_" + args.prec),
+                     "frac": achieved / hbm, "traffic": ncu_traffic("massive_" + args.prec + ("_force0" if args.force == 0 else "")),
                      "peak_kind": hbm_kind, "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": world * sites * args.steps / (e2e_ms / 1e3) / 1e9, "unit": "GLUPS",
                 "h2d_bytes_per_step": field_bytes / args.steps,
