@@ -506,7 +506,7 @@ __device__ __forceinline__ void relax_shells_paired(float R0, float R1, float R2
 // collide_store() with FP32 arithmetic (FP32 and 16-bit storage) on register
 // pairs: the same quantities in the same order of operations per population,
 // with each instruction serving two directions or two shells.
-template <typename S, int FORCE, int RES, class C>
+template <typename S, int FORCE, int RES, int BT, class C>
 __device__ __forceinline__ void collide_store_paired(float (&f)[kQ], S* __restrict__ fout,
                                                      const DevSample& s, int x, int y,
                                                      const StepAux<float>& aux, const C& qc,
@@ -517,7 +517,7 @@ __device__ __forceinline__ void collide_store_paired(float (&f)[kQ], S* __restri
   float egx = 0.f, egy = 0.f;
   if (lca) lca_gradient(s, dn_prev, x, y, egx, egy);
   const Moments<float> m = moments(f, qc);
-  const uint32_t park_stride = blockDim.x * 16u;
+  constexpr uint32_t park_stride = BT * 16u;
 #pragma unroll
   for (int d = 0; d < kDirs; ++d) park_store(park + d * park_stride, &f[4 * d]);
   Macro<float> M;
@@ -613,7 +613,7 @@ __device__ __forceinline__ void collide_store_paired(float (&f)[kQ], S* __restri
 // residual; 2 add |u - u_prev|^2 and |u|^2 to r_du2, r_u2 (the caller
 // reduces them).  dn_prev / dn_next: the electric force's density planes of
 // the previous and of this step (used when s.inv_cg != 0).
-template <typename S, int FORCE, int RES, class C>
+template <typename S, int FORCE, int RES, int BT, class C>
 __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* __restrict__ fout,
                                               const DevSample& s, int x, int y,
                                               const StepAux<typename Codec<S>::R>& aux,
@@ -623,7 +623,7 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
                                               typename Codec<S>::R* dn_next) {
   using R = typename Codec<S>::R;
   if constexpr (std::is_same<R, float>::value) {
-    collide_store_paired<S, FORCE, RES>(f, fout, s, x, y, aux, qc, r_du2, r_u2, park, dn_prev,
+    collide_store_paired<S, FORCE, RES, BT>(f, fout, s, x, y, aux, qc, r_du2, r_u2, park, dn_prev,
                                         dn_next);
     return;
   }
@@ -641,8 +641,8 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
     R egx = R(0), egy = R(0);
     if (lca) lca_gradient(s, dn_prev, x, y, egx, egy);
     const Moments<R> m = moments(f, qc);
-    // park: entry of direction d at park + d * blockDim.x * 16
-    const uint32_t park_stride = blockDim.x * 16u;
+    // park: entry of direction d at park + d * BT * 16 (BT threads per block)
+    constexpr uint32_t park_stride = BT * 16u;
     if constexpr (Park<R>::kOn) {
 #pragma unroll
       for (int d = 0; d < kDirs; ++d) park_store(park + d * park_stride, &f[4 * d]);
@@ -746,7 +746,7 @@ __device__ __forceinline__ void collide_store(typename Codec<S>::R (&f)[kQ], S* 
 }
 
 // Fused stream + collide of site (x, y) (nothing if x >= nx).
-template <typename S, int FORCE, int RES, class C>
+template <typename S, int FORCE, int RES, int BT, class C>
 __device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restrict__ fout,
                                           const DevSample& s, int x, int y,
                                           const typename Codec<S>::R* __restrict__ ghost,
@@ -759,7 +759,7 @@ __device__ __forceinline__ void site_step(const S* __restrict__ fin, S* __restri
     // select, not s.dn[cur]: a runtime index would move the descriptor to local memory
     void* const prev = cur ? s.dn[1] : s.dn[0];
     void* const next = cur ? s.dn[0] : s.dn[1];
-    collide_store<S, FORCE, RES>(f, fout, s, x, y, aux, qc, r_du2, r_u2, park,
+    collide_store<S, FORCE, RES, BT>(f, fout, s, x, y, aux, qc, r_du2, r_u2, park,
                                  static_cast<const R*>(prev), static_cast<R*>(next));
   }
 }
@@ -772,7 +772,7 @@ __device__ __forceinline__ void step_body(const S* __restrict__ fin, S* __restri
                                           const StepAux<typename Codec<S>::R>& aux, const C& qc,
                                           unsigned char* park) {
   double r_du2 = 0.0, r_u2 = 0.0;
-  site_step<S, FORCE, RES>(fin, fout, s, blockIdx.x * kBX + threadIdx.x, blockIdx.y, ghost, aux,
+  site_step<S, FORCE, RES, kBX>(fin, fout, s, blockIdx.x * kBX + threadIdx.x, blockIdx.y, ghost, aux,
                            qc, r_du2, r_u2, smem_addr(park) + threadIdx.x * 16u, s.cur);
   if (RES == 2) block_reduce_add2<typename Codec<S>::R>(r_du2, r_u2, aux.acc);
 }
@@ -813,7 +813,7 @@ __device__ __forceinline__ void batch_body(S* __restrict__ base, const BatchArgs
     const long long oin = b.cur ? s.off[1] : s.off[0];
     const long long oout = b.cur ? s.off[0] : s.off[1];
     double r_du2 = 0.0, r_u2 = 0.0;
-    site_step<S, FORCE, RES>(base + oin, base + oout, s, x, y,
+    site_step<S, FORCE, RES, BX>(base + oin, base + oout, s, x, y,
                              ghost + (long long)lo * kMaxContacts * kQ, aux, qc, r_du2, r_u2,
                              my_park, b.cur);
     // per-sample residual accumulators: acc[2 k], acc[2 k + 1]
@@ -933,7 +933,7 @@ __device__ __forceinline__ void staged_batch_body(S* __restrict__ base, const Ba
     }
     double r_du2 = 0.0, r_u2 = 0.0;
     if (x < s.nx)
-      collide_store<S, FORCE, RES>(f, base + (b.cur ? s.off[0] : s.off[1]), s, x, tl.z, aux, qc,
+      collide_store<S, FORCE, RES, BX>(f, base + (b.cur ? s.off[0] : s.off[1]), s, x, tl.z, aux, qc,
                                    r_du2, r_u2, my_park,
                                    static_cast<const R*>(b.cur ? s.dn[1] : s.dn[0]),
                                    static_cast<R*>(b.cur ? s.dn[0] : s.dn[1]));
