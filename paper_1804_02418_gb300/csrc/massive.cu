@@ -358,6 +358,41 @@ __device__ __forceinline__ void eq_pair(const EqSite<R>& e, int p, R& even, R& o
   odd = od;
 }
 
+// Couples of pairs with the same axis pattern (both on the x axis, both on
+// the y axis, or both off the axes), so that every term eq_pair() skips for
+// one pair is skipped for the other: the FP32 collision evaluates g^eq of a
+// couple on register pairs, lanes (first pair, second pair).
+constexpr int kCouples = kPairs / 2;
+__host__ __device__ constexpr int couple_a(int q) {
+  return q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 2 : q == 3 ? 6 : q == 4 ? 8 : q == 5 ? 10 : q == 6 ? 12 : q == 7 ? 13 : q == 8 ? 14 : q == 9 ? 16 : 18;
+}
+__host__ __device__ constexpr int couple_b(int q) {
+  return q == 0 ? 4 : q == 1 ? 5 : q == 2 ? 3 : q == 3 ? 7 : q == 4 ? 9 : q == 5 ? 11 : q == 6 ? 20 : q == 7 ? 21 : q == 8 ? 15 : q == 9 ? 17 : 19;
+}
+constexpr bool couples_valid() {
+  int seen[kPairs] = {};
+  for (int q = 0; q < kCouples; ++q) {
+    const int a = couple_a(q), b = couple_b(q);
+    if ((pair_x(a) == 0) != (pair_x(b) == 0) || (pair_y(a) == 0) != (pair_y(b) == 0)) return false;
+    ++seen[a];
+    ++seen[b];
+  }
+  for (int p = 0; p < kPairs; ++p)
+    if (seen[p] != 1) return false;
+  return true;
+}
+static_assert(couples_valid(), "every pair in one couple, both pairs of a couple alike on the axes");
+
+// eq_pair()'s FP32 tables of couple q as pairs (first pair, second pair)
+struct MCoupleConsts {
+  float2 LT[kCouples], LX[kCouples], LY[kCouples];
+  float2 WE[kCouples][5], WO[kCouples][4], BE[kCouples][8], BO[kCouples][8];
+  // and the FP32 collision's per-pair constants: vx, vy, mvE[.][1..4], mvO[.][0..1]
+  float2 vx[kCouples], vy[kCouples];
+  float2 p0[kCouples], px2[kCouples], pxy[kCouples], py2[kCouples], pxv[kCouples], pyv[kCouples];
+};
+__constant__ MCoupleConsts c_cp;
+
 template <typename R>
 __device__ __forceinline__ R eq_rest(const EqSite<R>& e) {
   const MConsts<R>& c = mc<R>();
@@ -449,41 +484,54 @@ __constant__ float2 c_mp = {-1.f, 1.f};
 
 __device__ __forceinline__ float2 S2(float a) { return make_float2(a, a); }
 
+// eq_pair() of the two pairs of couple q at once (lanes: couple_a(q),
+// couple_b(q)): the same terms in the same order on each lane.
+__device__ __forceinline__ void eq_couple(const EqSite<float>& e, int q, float2& even,
+                                          float2& odd) {
+  const int p = couple_a(q);   // the couple's axis pattern
+  float2 ev = __ffma2_rn(c_cp.LT[q], S2(e.dT), S2(e.dn));
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+    if (live(p, we_odd(k), we_odd(k))) ev = __ffma2_rn(c_cp.WE[q][k], S2(e.qE[k]), ev);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (live(p, be_odd(k), be_odd(k))) ev = __ffma2_rn(c_cp.BE[q][k], S2(e.E[k]), ev);
+  float2 od = S2(0.f);
+  if (pair_x(p) != 0) od = __ffma2_rn(c_cp.LX[q], S2(e.ux), od);
+  if (pair_y(p) != 0) od = __ffma2_rn(c_cp.LY[q], S2(e.uy), od);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (live(p, wo_x(k), !wo_x(k))) od = __ffma2_rn(c_cp.WO[q][k], S2(e.qO[k]), od);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (live(p, bo_x(k), !bo_x(k))) od = __ffma2_rn(c_cp.BO[q][k], S2(e.O[k]), od);
+  even = ev;
+  odd = od;
+}
+
 // mcollide_store for FP32 on register pairs (lanes: population 2p and its
 // opposite 2p + 1): the same quantities in the same order of operations per
-// population, two populations per paired FMA (Blackwell's FFMA2).
+// population, two populations per paired FMA (Blackwell's FFMA2); g^eq of
+// two pairs at a time (eq_couple).
 template <bool FORCE>
 __device__ __forceinline__ void mcollide_store_paired(const float (&g)[kQm], const MMacro<float>& M,
                                                       float inv_tau, float Fx, float Fy,
                                                       float* __restrict__ out, long long plane) {
-  const MConsts<float>& c = mc<float>();
   const EqSite<float> e = eq_site(M);
   const float gt = M.gamma * inv_tau;
   const float gux = gt * M.ux, guy = gt * M.uy;
   ForceSite<float> fs;
   if (FORCE) fs = force_site(M, Fx, Fy);
-#pragma unroll
-  for (int p = 0; p < kPairs; ++p) {
-    float ev, od;
-    eq_pair(e, p, ev, od);
-    float wv = 0.f;
-    if (pair_x(p) != 0) wv = gux * c.vx[p];
-    if (pair_y(p) != 0) wv = fmaf(guy, c.vy[p], wv);
+  // relaxation, force and store of pair p from the even / odd parts of its
+  // g^eq, v.u gamma / tau (wv) and the force's per-pair scalars
+  auto relax_pair = [&](const int p, const float ev, const float od, const float wv,
+                        const float Ae, const float He, const float Ao, const float Ho,
+                        const float Fv) {
     const float2 om = __ffma2_rn(S2(wv), c_mp, S2(gt));       // gamma (1 -+ v.u) / tau
     const float2 gpn = __ffma2_rn(S2(od), c_pm, S2(ev));      // (ev + od, ev - od)
     const float2 G = make_float2(g[2 * p], g[2 * p + 1]);
     float2 o = __ffma2_rn(om, __ffma2_rn(G, S2(-1.f), gpn), G);
     if (FORCE) {
-      const float px2 = c.mvE[p][2], pxy = c.mvE[p][3], py2 = c.mvE[p][4], p0 = c.mvE[p][1];
-      const float pxv = c.mvO[p][0], pyv = c.mvO[p][1];
-      float Ae = fmaf(fs.a5, px2, fs.a1), Ao = 0.f, He = fmaf(fs.hp0, p0, fs.h1), Ho = 0.f;
-      Ae = fmaf(fs.a6, pxy, fmaf(fs.a7, py2, Ae));
-      He = fmaf(fs.hxx, px2, fmaf(fs.hxy, pxy, fmaf(fs.hyy, py2, He)));
-      if (pair_x(p) != 0) { Ao = fs.a10 * pxv; Ho = fmaf(fmaf(fs.h0x, p0, fs.hx), pxv, Ho); }
-      if (pair_y(p) != 0) { Ao = fmaf(fs.a11, pyv, Ao); Ho = fmaf(fmaf(fs.h0y, p0, fs.hy), pyv, Ho); }
-      float Fv = 0.f;
-      if (pair_x(p) != 0) Fv = Fx * c.vx[p];
-      if (pair_y(p) != 0) Fv = fmaf(Fy, c.vy[p], Fv);
       // lanes: +-Fv (1 + g^eq -/+ ... - Ae -+ Ao) - He -+ Ho
       const float2 X = __ffma2_rn(S2(Ao), c_mp, __fadd2_rn(gpn, S2(1.f - Ae)));
       o = __ffma2_rn(S2(Fv), __fmul2_rn(X, c_pm), o);
@@ -491,6 +539,38 @@ __device__ __forceinline__ void mcollide_store_paired(const float (&g)[kQm], con
     }
     out[(long long)(2 * p) * plane] = o.x;
     out[(long long)(2 * p + 1) * plane] = o.y;
+  };
+  // the per-pair scalars of a couple on register pairs (lanes: couple_a(q),
+  // couple_b(q)), each lane with the operations of one pair in their order
+#pragma unroll
+  for (int q = 0; q < kCouples; ++q) {
+    const int p = couple_a(q);   // the couple's axis pattern
+    const bool hx = pair_x(p) != 0, hy = pair_y(p) != 0;
+    float2 ev, od;
+    eq_couple(e, q, ev, od);
+    float2 wv = S2(0.f);
+    if (hx) wv = __fmul2_rn(S2(gux), c_cp.vx[q]);
+    if (hy) wv = __ffma2_rn(S2(guy), c_cp.vy[q], wv);
+    float2 Ae = S2(0.f), He = S2(0.f), Ao = S2(0.f), Ho = S2(0.f), Fv = S2(0.f);
+    if (FORCE) {
+      const float2 px2 = c_cp.px2[q], pxy = c_cp.pxy[q], py2 = c_cp.py2[q], p0 = c_cp.p0[q];
+      Ae = __ffma2_rn(S2(fs.a5), px2, S2(fs.a1));
+      He = __ffma2_rn(S2(fs.hp0), p0, S2(fs.h1));
+      Ae = __ffma2_rn(S2(fs.a6), pxy, __ffma2_rn(S2(fs.a7), py2, Ae));
+      He = __ffma2_rn(S2(fs.hxx), px2, __ffma2_rn(S2(fs.hxy), pxy, __ffma2_rn(S2(fs.hyy), py2, He)));
+      if (hx) {
+        Ao = __fmul2_rn(S2(fs.a10), c_cp.pxv[q]);
+        Ho = __ffma2_rn(__ffma2_rn(S2(fs.h0x), p0, S2(fs.hx)), c_cp.pxv[q], Ho);
+      }
+      if (hy) {
+        Ao = __ffma2_rn(S2(fs.a11), c_cp.pyv[q], Ao);
+        Ho = __ffma2_rn(__ffma2_rn(S2(fs.h0y), p0, S2(fs.hy)), c_cp.pyv[q], Ho);
+      }
+      if (hx) Fv = __fmul2_rn(S2(Fx), c_cp.vx[q]);
+      if (hy) Fv = __ffma2_rn(S2(Fy), c_cp.vy[q], Fv);
+    }
+    relax_pair(couple_a(q), ev.x, od.x, wv.x, Ae.x, He.x, Ao.x, Ho.x, Fv.x);
+    relax_pair(couple_b(q), ev.y, od.y, wv.y, Ae.y, He.y, Ao.y, Ho.y, Fv.y);
   }
   const float gr = eq_rest(e);
   float orr = fmaf(gt, gr - g[kRestPop], g[kRestPop]);
@@ -557,9 +637,9 @@ __device__ __forceinline__ unsigned check_bits(const MMacro<R>& M, bool conv) {
 // Kernels (blocks of 32 x 4 sites)
 // ---------------------------------------------------------------------------
 template <typename R, bool FORCE>
-__global__ void __launch_bounds__(128) k_mstep(const R* __restrict__ src, R* __restrict__ dst,
-                                               MGeom geo, R inv_tau, R Fx, R Fy,
-                                               unsigned* __restrict__ err) {
+__device__ __forceinline__ void mstep_body(const R* __restrict__ src, R* __restrict__ dst,
+                                           const MGeom& geo, R inv_tau, R Fx, R Fy,
+                                           unsigned* __restrict__ err) {
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 4 + threadIdx.y;
   if (x >= geo.nx || y >= geo.ny) return;
   R g[kQm];
@@ -571,6 +651,22 @@ __global__ void __launch_bounds__(128) k_mstep(const R* __restrict__ src, R* __r
   const unsigned bits = check_bits(M, conv);
   mcollide_store<R, FORCE>(g, M, inv_tau, Fx, Fy, dst + (long long)y * geo.ldx + x, geo.plane);
   if (bits) atomicOr(err, bits);
+}
+
+template <typename R, bool FORCE>
+__global__ void __launch_bounds__(128) k_mstep(const R* __restrict__ src, R* __restrict__ dst,
+                                               MGeom geo, R inv_tau, R Fx, R Fy,
+                                               unsigned* __restrict__ err) {
+  mstep_body<R, FORCE>(src, dst, geo, inv_tau, Fx, Fy, err);
+}
+
+// FP32 with the force: at most 128 registers, so that 4 blocks stay resident
+// per SM (the paired equilibrium would otherwise take 130 and leave room for 3).
+__global__ void __launch_bounds__(128, 4) k_mstep_f32_force(const float* __restrict__ src,
+                                                            float* __restrict__ dst, MGeom geo,
+                                                            float inv_tau, float Fx, float Fy,
+                                                            unsigned* __restrict__ err) {
+  mstep_body<float, true>(src, dst, geo, inv_tau, Fx, Fy, err);
 }
 
 template <typename R>
@@ -691,6 +787,30 @@ void fill_consts(const Tables& t, MConsts<R>& c) {
   for (int i = 0; i < kQm; ++i) c.f0[i] = t.f0[i];
 }
 
+// the FP32 tables of the collision rearranged by couple (the same float values)
+void fill_couples(const MConsts<float>& c, MCoupleConsts& h) {
+  for (int q = 0; q < kCouples; ++q) {
+    const int a = couple_a(q), b = couple_b(q);
+    h.LT[q] = make_float2(c.LT[a], c.LT[b]);
+    h.LX[q] = make_float2(c.LX[a], c.LX[b]);
+    h.LY[q] = make_float2(c.LY[a], c.LY[b]);
+    for (int k = 0; k < 5; ++k) h.WE[q][k] = make_float2(c.WE[a][k], c.WE[b][k]);
+    for (int k = 0; k < 4; ++k) h.WO[q][k] = make_float2(c.WO[a][k], c.WO[b][k]);
+    for (int k = 0; k < 8; ++k) {
+      h.BE[q][k] = make_float2(c.BE[a][k], c.BE[b][k]);
+      h.BO[q][k] = make_float2(c.BO[a][k], c.BO[b][k]);
+    }
+    h.vx[q] = make_float2(c.vx[a], c.vx[b]);
+    h.vy[q] = make_float2(c.vy[a], c.vy[b]);
+    h.p0[q] = make_float2(c.mvE[a][1], c.mvE[b][1]);
+    h.px2[q] = make_float2(c.mvE[a][2], c.mvE[b][2]);
+    h.pxy[q] = make_float2(c.mvE[a][3], c.mvE[b][3]);
+    h.py2[q] = make_float2(c.mvE[a][4], c.mvE[b][4]);
+    h.pxv[q] = make_float2(c.mvO[a][0], c.mvO[b][0]);
+    h.pyv[q] = make_float2(c.mvO[a][1], c.mvO[b][1]);
+  }
+}
+
 std::mutex g_upload_mu;
 bool g_uploaded[64];
 
@@ -737,10 +857,13 @@ int upload_tables(int dev) {
   if (g_uploaded[dev]) return RLBM_OK;
   static MConsts<float> hf;
   static MConsts<double> hd;
+  static MCoupleConsts hc;
   fill_consts(t, hf);
   fill_consts(t, hd);
+  fill_couples(hf, hc);
   cudaError_t e = cudaMemcpyToSymbol(c_f, &hf, sizeof hf);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_d, &hd, sizeof hd);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cp, &hc, sizeof hc);
   if (e != cudaSuccess) return fail(nullptr, RLBM_ECUDA, "constant upload: %s", cudaGetErrorString(e));
   g_uploaded[dev] = true;
   return RLBM_OK;
@@ -781,7 +904,7 @@ int launch_steps(rlbm_massive_ctx* c, int nsteps) {
       else k_mstep<double, false><<<grid, block, 0, stream_of(c)>>>((const double*)src, (double*)dst, c->geo, it, fx, fy, c->err);
     } else {
       const float it = (float)(1.0 / c->cfg.tau), fx = (float)c->cfg.Fx, fy = (float)c->cfg.Fy;
-      if (force) k_mstep<float, true><<<grid, block, 0, stream_of(c)>>>((const float*)src, (float*)dst, c->geo, it, fx, fy, c->err);
+      if (force) k_mstep_f32_force<<<grid, block, 0, stream_of(c)>>>((const float*)src, (float*)dst, c->geo, it, fx, fy, c->err);
       else k_mstep<float, false><<<grid, block, 0, stream_of(c)>>>((const float*)src, (float*)dst, c->geo, it, fx, fy, c->err);
     }
     cudaError_t e = cudaGetLastError();
